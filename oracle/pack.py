@@ -24,7 +24,9 @@ Format (little-endian).  One package per stored block of an operator class
     32   i16   q_out.n, i16 q_out.tsz, i16 q_in.n, i16 q_in.tsz
     40   u32   rows
     44   u32   cols
-    48   u64   element offset of the block in the unpacked arena
+    48   u64   element offset of the block in the unpacked arena (blocks
+               follow each other in canonical order, each padded to an even
+               number of float64 so that every block starts 16-byte aligned)
     56   u64   checksum
     64   ...   payload: layers*rows*cols float64, row-major per layer,
                zero-padded to a multiple of 16 bytes
@@ -57,14 +59,17 @@ def checksum(payload: bytes) -> int:
 
 
 def canonical_blocks(classes):
-    """Flatten classes into (class index, block) in canonical order with arena offsets."""
+    """Flatten classes into (class index, block) in canonical order with arena offsets.
+
+    Returns the list and the arena length in float64 elements.
+    """
     out = []
     off = 0
     for ci, cl in enumerate(classes):
         nl = len(cl["layers"])
         for (qo, qi, r, c, data) in cl["blocks"]:
             out.append((ci, nl, qo, qi, r, c, data, off))
-            off += nl * r * c
+            off += (nl * r * c + 1) // 2 * 2
     return out, off
 
 
@@ -102,6 +107,15 @@ def split_packages(stream: bytes):
         size = 64 + pad16(nl * r * c * 8)
         out.append(stream[o:o + size])
         o += size
+    return out
+
+
+def arena(classes):
+    """The unpacked arena of an environment: blocks in canonical order, padded."""
+    blocks, n = canonical_blocks(classes)
+    out = np.zeros(n)
+    for (_, nl, _, _, r, c, data, off) in blocks:
+        out[off:off + nl * r * c] = np.asarray(data, dtype=np.float64).ravel()
     return out
 
 

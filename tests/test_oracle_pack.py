@@ -28,8 +28,8 @@ def test_round_trip_bit_exact_and_size_prediction(seed):
     assert len(s) == total
     assert all(o % 16 == 0 for o in offsets)
     arena = P.unpack(s, arena_n)
-    flat = np.concatenate([b[6].ravel() for b in blocks]) if blocks else np.zeros(0)
-    assert arena.tobytes() == flat.tobytes()
+    assert arena.tobytes() == P.arena(cls).tobytes()
+    assert all(b[7] % 2 == 0 for b in blocks)
 
 
 def test_order_independent_reassembly():
