@@ -1,0 +1,232 @@
+/*
+ * gbdmrg.h -- C ABI of a single-GPU (GB300, sm_103a) two-site DMRG hot path:
+ * block-sparse effective-Hamiltonian products inside Davidson, truncation,
+ * renormalisation, sweeps, and the parallel pack/unpack (serialise /
+ * deserialise) of block-sparse environments with host offload.
+ *
+ * Method: arXiv:2412.04676.  Eq. 1 (Hamiltonian), Eq. 2 (MPS), Eq. 3
+ * (variational minimum), Sec. II.B (two-site step: pre-processing,
+ * diagonalisation, post-processing; Fig. 3a), Sec. III.A (asynchronous save),
+ * Sec. III.B.2 (exact-size parallel serialisation), Sec. III.B.3
+ * (self-contained packages), Sec. III.B.4 (load-after-renormalise ordering).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Orbitals (sites) 0..L-1.  Local basis per orbital: 0=|0>, 1=|up>, 2=|dn>,
+ * 3=|updn> = c+_up c+_dn |0>.  Quantum numbers q = (n, tsz), tsz = twice S_z,
+ * counted from the left: bond (cut) k carries those of orbitals 0..k-1.
+ * The two-site step at site b works on orbitals (b, b+1); its enlarged left
+ * block is (cut-b block + orbital b), its enlarged right block is
+ * (orbital b+1 + cut-(b+2) block).
+ *
+ * Wavefunction layout ("sector-major"): sectors Q of the enlarged left block
+ * that also exist on the enlarged right block, in ascending (n, tsz)
+ * lexicographic order; each sector is a row-major dense matrix
+ * rows = dim of the enlarged left block in Q, cols = dim of the enlarged
+ * right block in Q.  Rows list the local states s = 0..3 in order, each
+ * followed by the states of cut-b sector Q - q_s; columns list s = 0..3 in
+ * order, each followed by the states of cut-(b+2) sector Q + q_s.
+ *
+ * Status: every call returns int: 0 = OK, < 0 = error, > 0 = warning.
+ * gbd_last_error() gives a thread-local message for the last failure.  No
+ * exception crosses the ABI and no device code traps.
+ *
+ * Ownership: the library owns all device memory and pinned host memory it
+ * allocates; callers own every array they pass in, which is copied (or fully
+ * consumed) before the call returns unless a comment says otherwise.
+ * Device pointers passed in must stay valid for the duration of the call.
+ */
+#ifndef GBDMRG_H
+#define GBDMRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GBD_OK = 0,
+    GBD_ERR_ARG = -1,          /* bad argument, size or state of inputs         */
+    GBD_ERR_DEVICE_OOM = -2,   /* cudaMalloc failed                              */
+    GBD_ERR_HOST_OOM = -3,     /* pinned host allocation failed                  */
+    GBD_ERR_CUDA = -4,         /* any other CUDA / cuSOLVER error                */
+    GBD_ERR_TIMEOUT = -5,      /* a bounded wait on an IO event ran out          */
+    GBD_ERR_CORRUPT = -6,      /* package magic / checksum / metadata mismatch   */
+    GBD_ERR_STATE = -7,        /* call out of order (e.g. no integrals loaded)   */
+    GBD_WARN_NOT_CONVERGED = 1 /* Davidson hit its product limit                 */
+};
+
+enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1 };
+
+typedef struct gbd_ctx gbd_ctx;
+
+typedef struct {
+    int L;              /* orbitals                                             */
+    int N;              /* electrons                                            */
+    int tsz;            /* twice S_z                                            */
+    int D;              /* maximum kept states per bond (truncation)            */
+    int precision;      /* GBD_FP64 or GBD_MIXED_BF16X3 (H_eff products only)   */
+    double dav_tol;     /* Davidson residual norm tolerance (FP64 norm)         */
+    int dav_max_sub;    /* Davidson subspace size before restart                */
+    int dav_keep;       /* Ritz vectors kept at restart                         */
+    int dav_max_matvec; /* product limit -> GBD_WARN_NOT_CONVERGED              */
+    int offload;        /* 1: environments are packed to pinned host RAM after
+                           creation and unpacked on demand (Sec. III.A)       */
+    int device;         /* CUDA device ordinal                                  */
+    int switch_cut;     /* cut from which two-operator sets are stored as
+                           complementary sums; 0 = automatic (L/2 + 1)         */
+    int io_timeout_ms;  /* bound on any host wait for an IO event              */
+    unsigned long long seed; /* random initial MPS when none is imported       */
+} gbd_config;
+
+typedef struct {
+    int n, tsz;         /* quantum numbers of the sector                        */
+    int rows, cols;     /* enlarged-left dim x enlarged-right dim               */
+    long long offset;   /* element offset in the sector-major vector            */
+} gbd_sector_info;
+
+typedef struct {
+    long long dim;          /* length of the wavefunction vector                */
+    int n_sectors;
+    int n_terms;            /* operator pairs (MPO states at the centre cut)    */
+    int n_classes;          /* groups of terms sharing one block structure       */
+    long long n_gemm;       /* sector GEMMs in one product (both phases)         */
+    double useful_flops;    /* 2*m*k*n summed over those GEMMs, counted once     */
+    double operator_bytes;  /* FP64 bytes of the two enlarged operator sets      */
+} gbd_heff_info;
+
+typedef struct {
+    double energy;
+    double resid;
+    int matvecs;
+    int iterations;
+    double ms_matvec;       /* device time spent in H_eff products               */
+} gbd_dav_stats;
+
+typedef struct {
+    double energy_last;     /* Davidson energy at the last step of the sweep     */
+    double energy_min;      /* minimum over the sweep                            */
+    double max_trunc;       /* largest truncation weight in the sweep            */
+    int matvecs;
+    double ms_total;        /* wall time of the sweep                            */
+    double ms_matvec;       /* H_eff products                                    */
+    double ms_davidson;     /* Davidson excluding products                       */
+    double ms_truncate;     /* density matrix, eigensolver, selection            */
+    double ms_renorm;       /* enlargement + renormalisation                     */
+    double ms_io_exposed;   /* host waits on IO events                           */
+    double bytes_packed;    /* serialised environment bytes                      */
+    double ms_pack;         /* device time of pack kernels                       */
+    double useful_flops;    /* H_eff useful flops over the sweep                 */
+} gbd_sweep_stats;
+
+/* ---------------------------------------------------------------- lifecycle */
+int gbd_config_default(gbd_config* cfg);
+int gbd_create(const gbd_config* cfg, gbd_ctx** out);
+void gbd_destroy(gbd_ctx* ctx);
+const char* gbd_last_error(void);
+int gbd_version(void);
+
+/* -------------------------------------------------------------------- model */
+/* Eq. 1 with chemist integrals: H = sum h_ij a+_is a_js
+ *   + 1/2 sum (ij|kl) a+_is a+_kt a_lt a_js + e_core.
+ * h: L*L row-major, symmetric; eri: L^4 row-major (ij|kl), 8-fold symmetric.
+ * Symmetry is checked to 1e-12 (relative to the largest element) -> GBD_ERR_ARG.
+ * Builds the left/right operator sets of every cut (host tables). */
+int gbd_load_integrals(gbd_ctx* ctx, int L, const double* h, const double* eri, double e_core);
+
+/* Number of operator pairs (MPO states) at cut c (0..L). */
+int gbd_mpo_bond_dim(gbd_ctx* ctx, int cut, int* dim);
+
+/* Host-only check for tiny L (<= 5): the operator sets contracted into the
+ * dense 4^L x 4^L matrix of Eq. 1 (row-major, orbital 0 most significant).
+ * out must hold 4^(2L) doubles.  No device work. */
+int gbd_mpo_dense(gbd_ctx* ctx, double* out, size_t cap);
+
+/* ---------------------------------------------------------------- MPS input */
+/* One site tensor (Eq. 2) as blocks.  meta: nblocks x 5 ints
+ * (q_left.n, q_left.tsz, s, rows, cols); data: the blocks row-major, one after
+ * another (host memory).  kind 0 = left-isometric, 1 = right-isometric.
+ * Bond dimensions are inferred from the blocks and must be consistent with
+ * neighbouring sites. */
+int gbd_import_site(gbd_ctx* ctx, int site, int kind, int nblocks, const int* meta, const double* data);
+
+/* Builds left environments for cuts 0..b and right environments for cuts
+ * L..b+2 from the imported sites (renormalisation, Sec. II.B step 3). */
+int gbd_build_envs(gbd_ctx* ctx, int b);
+
+/* --------------------------------------------------------------- tables a1 */
+/* Sector table of the wavefunction at two-site position b (needs
+ * gbd_build_envs or a sweep position at b).  Writes up to cap sectors to
+ * out, the count to *n, and the product statistics to *info. */
+int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n, gbd_heff_info* info);
+
+/* ------------------------------------------------------------ hot path a3 */
+/* psi_out = H_eff psi_in at position b (Sec. II.B step 2).  Vectors in the
+ * sector-major layout above, FP64.  on_device = 1: both pointers are device
+ * pointers; 0: host pointers (copied in and out).  precision selects the
+ * FP64 or BF16x3 product.  psi_out may not alias psi_in. */
+int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, int on_device, int precision);
+
+/* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
+int gbd_heff_diagonal(gbd_ctx* ctx, int b, double* diag, int on_device);
+
+/* ------------------------------------------------------------ Davidson a4 */
+/* Lowest eigenpair of H_eff at b.  psi (host, sector-major) is the start
+ * vector on entry (NULL = library's current two-site vector or random) and
+ * the normalised eigenvector on exit (may be NULL).  Returns
+ * GBD_WARN_NOT_CONVERGED if the product limit was reached. */
+int gbd_davidson(gbd_ctx* ctx, int b, double* psi, double* energy, gbd_dav_stats* stats);
+
+/* ------------------------------------------------------------ truncation a5 */
+/* Truncates the current two-site vector at b to at most Dmax states on the
+ * enlarged left (dir = +1) or right (dir = -1) block, renormalises the
+ * operators of that block (a6), and forms the next start vector. */
+int gbd_truncate(gbd_ctx* ctx, int b, int dir, int Dmax, double* trunc_weight);
+
+/* ------------------------------------------------------------------ sweep */
+/* nsweeps full sweeps (left-to-right over b = 0..L-3, right-to-left over
+ * b = L-2..1).  Starts from the imported MPS (all sites right-isometric) or
+ * from a seeded random one.  stats may be NULL; per-sweep stats are written
+ * to stats[i] for i < nsweeps. */
+int gbd_sweep(gbd_ctx* ctx, int nsweeps, int D, gbd_sweep_stats* stats);
+
+/* Current energies of the last sweep steps, one per step (host array). */
+int gbd_step_energies(gbd_ctx* ctx, double* out, int cap, int* n);
+
+/* ---------------------------------------------------------- pack a7, a8 */
+/* Environment ids: side 0 = left block (cut c, orbitals 0..c-1), side 1 =
+ * right block (cut c, orbitals c..L-1).
+ *
+ * gbd_pack_env serialises one resident environment into dst (host or device
+ * memory, flagged) as self-contained packages (format in the design doc of the
+ * source tree: 64-byte header + payload, 16-byte aligned, checksum).  If cap
+ * is too small, returns GBD_ERR_ARG and writes the exact required size to
+ * *bytes (size prediction, Sec. III.B.2).  */
+int gbd_pack_env(gbd_ctx* ctx, int side, int cut, void* dst, size_t cap, size_t* bytes, int dst_on_device);
+
+/* Deserialises packages (any order) into the resident environment with the
+ * same id, which must exist with the same block structure (its data are
+ * overwritten).  Bad magic, ids, dims or checksum -> GBD_ERR_CORRUPT. */
+int gbd_unpack_env(gbd_ctx* ctx, int side, int cut, const void* src, size_t bytes, int src_on_device);
+
+/* Imports a raw environment for pack tests: classes of layers sharing one
+ * block structure.  class_meta: ncls x 3 ints (dq.n, dq.tsz, n_layers);
+ * block_meta: nblk x 7 ints (class, q_out.n, q_out.tsz, q_in.n, q_in.tsz,
+ * rows, cols) in canonical order (class-major); data: the blocks one after
+ * another, each n_layers*rows*cols doubles (host). */
+int gbd_env_import(gbd_ctx* ctx, int side, int cut, int ncls, const int* class_meta, int nblk,
+                   const int* block_meta, const double* data);
+
+/* Copies a resident environment's arena to host (canonical order, each
+ * block padded to an even number of doubles).  *elems gets the arena size. */
+int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, size_t* elems);
+
+/* Offload statistics of the context so far. */
+int gbd_io_stats(gbd_ctx* ctx, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBDMRG_H */

@@ -1,0 +1,291 @@
+"""Python binding of libgbdmrg (ctypes): argument marshalling only.
+
+Every step of the two-site DMRG hot path runs inside the library's CUDA
+kernels; this module converts numpy arrays / torch tensors to plain pointers
+and status codes to exceptions.  The library must have been built in-tree
+(``paper_2412_04676_gb300/build.py``); there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
+HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
+
+FP64, MIXED_BF16X3 = 0, 1
+ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
+          -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
+WARN_NOT_CONVERGED = 1
+
+
+class GbdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("L", C.c_int), ("N", C.c_int), ("tsz", C.c_int), ("D", C.c_int), ("precision", C.c_int),
+                ("dav_tol", C.c_double), ("dav_max_sub", C.c_int), ("dav_keep", C.c_int),
+                ("dav_max_matvec", C.c_int), ("offload", C.c_int), ("device", C.c_int),
+                ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong)]
+
+
+class SectorInfo(C.Structure):
+    _fields_ = [("n", C.c_int), ("tsz", C.c_int), ("rows", C.c_int), ("cols", C.c_int), ("offset", C.c_longlong)]
+
+
+class HeffInfo(C.Structure):
+    _fields_ = [("dim", C.c_longlong), ("n_sectors", C.c_int), ("n_terms", C.c_int), ("n_classes", C.c_int),
+                ("n_gemm", C.c_longlong), ("useful_flops", C.c_double), ("operator_bytes", C.c_double)]
+
+
+class DavStats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int), ("iterations", C.c_int),
+                ("ms_matvec", C.c_double)]
+
+
+class SweepStats(C.Structure):
+    _fields_ = [("energy_last", C.c_double), ("energy_min", C.c_double), ("max_trunc", C.c_double),
+                ("matvecs", C.c_int), ("ms_total", C.c_double), ("ms_matvec", C.c_double),
+                ("ms_davidson", C.c_double), ("ms_truncate", C.c_double), ("ms_renorm", C.c_double),
+                ("ms_io_exposed", C.c_double), ("bytes_packed", C.c_double), ("ms_pack", C.c_double),
+                ("useful_flops", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "gbd_version": (C.c_int, []),
+    "gbd_last_error": (C.c_char_p, []),
+    "gbd_config_default": (C.c_int, [C.POINTER(Config)]),
+    "gbd_create": (C.c_int, [C.POINTER(Config), C.POINTER(_P)]),
+    "gbd_destroy": (None, [_P]),
+    "gbd_load_integrals": (C.c_int, [_P, C.c_int, _P, _P, C.c_double]),
+    "gbd_mpo_bond_dim": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "gbd_mpo_dense": (C.c_int, [_P, _P, C.c_size_t]),
+    "gbd_import_site": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "gbd_build_envs": (C.c_int, [_P, C.c_int]),
+    "gbd_build_tables": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(HeffInfo)]),
+    "gbd_apply_heff": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_int]),
+    "gbd_heff_diagonal": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "gbd_davidson": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double), C.POINTER(DavStats)]),
+    "gbd_truncate": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "gbd_sweep": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "gbd_step_energies": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
+    "gbd_pack_env": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t), C.c_int]),
+    "gbd_unpack_env": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.c_int]),
+    "gbd_env_import": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P]),
+    "gbd_env_export": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)]),
+}
+
+
+def declared_symbols():
+    """Names of the functions declared in include/gbdmrg.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_ ]+\*?\s*\**\s*(gbd_[a-z_]+)\s*\(", txt, re.M)))
+
+
+def lib():
+    """Load the in-tree library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgbdmrg.so not built ({LIB_PATH}); run paper_2412_04676_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        raise GbdError(rc, lib().gbd_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Pointer of a contiguous numpy array or torch tensor (host or device)."""
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data)
+
+
+def _on_device(a):
+    return int(bool(getattr(a, "is_cuda", False)))
+
+
+def site_arrays(site):
+    """Flatten a dict site tensor {(q_left, s): block} into (meta, data)."""
+    keys = sorted(site.keys())
+    meta = np.array([[q[0], q[1], s, site[(q, s)].shape[0], site[(q, s)].shape[1]] for (q, s) in keys],
+                    dtype=np.int32).reshape(-1, 5)
+    data = np.concatenate([np.ascontiguousarray(site[k], dtype=np.float64).ravel() for k in keys]) \
+        if keys else np.zeros(0)
+    return np.ascontiguousarray(meta), np.ascontiguousarray(data)
+
+
+class Context:
+    """One library context: integrals, MPS, environments, two-site position."""
+
+    def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
+                 dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345):
+        cfg = Config()
+        _check(lib().gbd_config_default(C.byref(cfg)))
+        cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
+        cfg.offload, cfg.device, cfg.dav_tol = int(offload), device, dav_tol
+        cfg.dav_max_sub, cfg.dav_keep, cfg.dav_max_matvec = dav_max_sub, dav_keep, dav_max_matvec
+        cfg.switch_cut, cfg.io_timeout_ms, cfg.seed = switch_cut, io_timeout_ms, seed
+        h = C.c_void_p()
+        _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.L, self.N, self.tsz = L, N, tsz
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gbd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- model
+    def load_integrals(self, h, eri, e_core=0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        _check(lib().gbd_load_integrals(self.h, h.shape[0], _ptr(h), _ptr(eri), e_core))
+
+    def mpo_bond_dim(self, cut):
+        d = C.c_int()
+        _check(lib().gbd_mpo_bond_dim(self.h, cut, C.byref(d)))
+        return d.value
+
+    def mpo_dense(self):
+        n = 4 ** self.L
+        out = np.zeros((n, n))
+        _check(lib().gbd_mpo_dense(self.h, _ptr(out), out.size))
+        return out
+
+    def import_mps(self, sites, kinds):
+        for k, (site, kind) in enumerate(zip(sites, kinds)):
+            meta, data = site_arrays(site)
+            _check(lib().gbd_import_site(self.h, k, kind, meta.shape[0], _ptr(meta), _ptr(data)))
+
+    def build_envs(self, b):
+        _check(lib().gbd_build_envs(self.h, b))
+
+    # ---------------------------------------------------------------- tables
+    def tables(self, b):
+        n = C.c_int()
+        info = HeffInfo()
+        _check(lib().gbd_build_tables(self.h, b, None, 0, C.byref(n), C.byref(info)))
+        arr = (SectorInfo * max(n.value, 1))()
+        _check(lib().gbd_build_tables(self.h, b, C.cast(arr, C.c_void_p), n.value, C.byref(n), C.byref(info)))
+        secs = [dict(q=(a.n, a.tsz), rows=a.rows, cols=a.cols, offset=a.offset) for a in arr[:n.value]]
+        return secs, {k: getattr(info, k) for k, _ in HeffInfo._fields_}
+
+    # ---------------------------------------------------------------- hot path
+    def apply_heff(self, b, x, out=None, precision=FP64):
+        if out is None:
+            out = np.zeros_like(x) if not hasattr(x, "data_ptr") else x.new_zeros(x.shape)
+        _check(lib().gbd_apply_heff(self.h, b, _ptr(x), _ptr(out), _on_device(x), precision))
+        return out
+
+    def heff_diagonal(self, b, dim):
+        d = np.zeros(dim)
+        _check(lib().gbd_heff_diagonal(self.h, b, _ptr(d), 0))
+        return d
+
+    def davidson(self, b, psi=None):
+        e = C.c_double()
+        st = DavStats()
+        p = None
+        if psi is not None:
+            psi = np.ascontiguousarray(psi, dtype=np.float64)
+            p = _ptr(psi)
+        rc = _check(lib().gbd_davidson(self.h, b, p, C.byref(e), C.byref(st)))
+        return e.value, psi, {k: getattr(st, k) for k, _ in DavStats._fields_}, rc
+
+    def truncate(self, b, direction, Dmax):
+        w = C.c_double()
+        _check(lib().gbd_truncate(self.h, b, direction, Dmax, C.byref(w)))
+        return w.value
+
+    def sweep(self, nsweeps, D):
+        st = (SweepStats * nsweeps)()
+        _check(lib().gbd_sweep(self.h, nsweeps, D, C.cast(st, C.c_void_p)))
+        return [s.as_dict() for s in st]
+
+    def step_energies(self):
+        n = C.c_int()
+        _check(lib().gbd_step_energies(self.h, None, 0, C.byref(n)))
+        out = np.zeros(max(n.value, 1))
+        _check(lib().gbd_step_energies(self.h, _ptr(out), n.value, C.byref(n)))
+        return out[:n.value]
+
+    # ---------------------------------------------------------------- pack
+    def pack_size(self, side, cut):
+        need = C.c_size_t()
+        rc = lib().gbd_pack_env(self.h, side, cut, None, 0, C.byref(need), 0)
+        if rc not in (0, -1):
+            _check(rc)
+        return need.value
+
+    def pack_env(self, side, cut, dst=None):
+        n = self.pack_size(side, cut)
+        if dst is None:
+            dst = np.zeros(n, dtype=np.uint8)
+        need = C.c_size_t()
+        nbytes = dst.numel() if hasattr(dst, "numel") else dst.nbytes
+        _check(lib().gbd_pack_env(self.h, side, cut, _ptr(dst), nbytes, C.byref(need), _on_device(dst)))
+        return dst
+
+    def unpack_env(self, side, cut, src):
+        nbytes = src.numel() if hasattr(src, "numel") else src.nbytes
+        _check(lib().gbd_unpack_env(self.h, side, cut, _ptr(src), nbytes, _on_device(src)))
+
+    def env_import(self, side, cut, classes):
+        """classes as produced by inputs.make_env_blocks (canonical order)."""
+        cm = np.array([[c["dq"][0], c["dq"][1], len(c["layers"])] for c in classes], dtype=np.int32).reshape(-1, 3)
+        bm, data = [], []
+        for ci, c in enumerate(classes):
+            for (qo, qi, r, cc, d) in c["blocks"]:
+                bm.append([ci, qo[0], qo[1], qi[0], qi[1], r, cc])
+                data.append(np.ascontiguousarray(d, dtype=np.float64).ravel())
+        bm = np.array(bm, dtype=np.int32).reshape(-1, 7)
+        data = np.concatenate(data) if data else np.zeros(0)
+        cm, bm, data = (np.ascontiguousarray(x) for x in (cm, bm, data))
+        _check(lib().gbd_env_import(self.h, side, cut, cm.shape[0], _ptr(cm), bm.shape[0], _ptr(bm), _ptr(data)))
+
+    def env_export(self, side, cut):
+        n = C.c_size_t()
+        rc = lib().gbd_env_export(self.h, side, cut, None, 0, C.byref(n))
+        if rc not in (0, -1):
+            _check(rc)
+        out = np.zeros(max(n.value, 1))
+        _check(lib().gbd_env_export(self.h, side, cut, _ptr(out), out.size, C.byref(n)))
+        return out[:n.value]
+
+    def io_stats(self):
+        v = [C.c_double() for _ in range(4)]
+        _check(lib().gbd_io_stats(self.h, *[C.byref(x) for x in v]))
+        return dict(bytes_d2h=v[0].value, bytes_h2d=v[1].value, ms_exposed=v[2].value, ms_pack=v[3].value)

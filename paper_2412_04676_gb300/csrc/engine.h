@@ -1,0 +1,123 @@
+// engine.h -- state of one library context and the host-side steps of the
+// two-site DMRG iteration (Sec. II.B of arXiv:2412.04676).
+#pragma once
+
+#include <cusolverDn.h>
+
+#include <memory>
+#include <vector>
+
+#include "core.h"
+#include "kernels.h"
+#include "mpo.h"
+#include "tc.h"
+
+namespace gbd {
+
+// A site tensor of Eq. 2 in isometric form.
+//  kind 0 (left): U_Q, rows = enlarged-left basis of bond k, cols = bond k+1 sector Q
+//  kind 1 (right): V_Q, rows = enlarged-right basis of bond k+1 (labelled at
+//  cut k), cols = bond k sector Q.
+struct Iso {
+    int kind = -1;
+    EBasis basis;
+    Bond out;
+    std::vector<long long> off;  // per out sector, -1 if absent
+    long long total = 0;
+    DevBuf data;
+    std::vector<double> host;    // host copy (imported or exported)
+};
+
+// Packed (serialised) copy of an environment in pinned host memory.
+struct HostEnv {
+    unsigned char* host = nullptr;   // packages (mapped pinned)
+    size_t cap = 0, bytes = 0;
+    bool valid = false;              // holds a complete save
+    cudaEvent_t done = nullptr;      // last save into `host` finished
+    int npk = 0;
+    unsigned char* meta = nullptr;   // pack/unpack item + chunk tables (mapped pinned)
+    size_t meta_cap = 0;
+    unsigned long long* cks_dev = nullptr;   // per-package checksum accumulators
+    unsigned long long* cks_host = nullptr;  // verification copy (pinned)
+    size_t cks_cap = 0;
+    bool pending = false;            // load enqueued, not yet verified
+    cudaEvent_t loaded = nullptr;
+    std::vector<unsigned long long> want;
+};
+
+// Enlarged operators and product plans at one two-site position b.
+struct Heff {
+    int b = -1;
+    EBasis bL, bR;
+    std::vector<Q> sq;
+    std::vector<int> sL, sR;
+    std::vector<long long> soff;
+    long long dim = 0;
+    OpSet OL, OR;
+    GemmPlan p1, p2;
+    DevBuf X, xin, yout, diag;
+    bool diag_ready = false;
+    long long ngemm = 0;
+    double flops = 0.0, op_bytes = 0.0;
+    TcHeff tc;               // mixed-precision (BF16x3, tcgen05) operands and plans
+    bool tc_ready = false;
+    int sector_of(const Q& q) const {
+        auto it = std::lower_bound(sq.begin(), sq.end(), q);
+        if (it == sq.end() || *it != q) return -1;
+        return int(it - sq.begin());
+    }
+};
+
+struct Ctx {
+    gbd_config cfg{};
+    bool have_ints = false, cuda_ready = false;
+    int L = 0;
+    std::vector<double> h, eri;
+    double ecore = 0.0;
+    Mpo mpo;
+    std::vector<Bond> bonds;
+    std::vector<Iso> sites;
+    std::vector<std::vector<double>> site_blocks_data;
+    std::vector<std::vector<int>> site_blocks_meta;
+    std::vector<int> site_kind;
+    std::vector<std::unique_ptr<OpSet>> envL, envR;
+    std::vector<HostEnv> hostL, hostR;
+    cudaStream_t cs = nullptr, ios = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    Heff H;
+    DevBuf psi;
+    bool psi_valid = false;
+    int psi_b = -1;
+    // scratch
+    GemmPlan plan_a, plan_b, plan_c;
+    DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small;
+    DevBuf dav_V, dav_AV, dav_r, dav_t, dav_x, dav_ax, dav_tmp;
+    DevBuf stage;  // device staging for pack/unpack through pageable memory
+    // statistics
+    std::vector<double> step_energy;
+    double io_d2h = 0, io_h2d = 0, io_exposed_ms = 0, pack_ms = 0;
+    double ms_matvec_acc = 0;
+    int matvec_count = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+void ensure_cuda(Ctx& C);
+void destroy_ctx(Ctx& C);
+void load_integrals(Ctx& C, int L, const double* h, const double* eri, double ecore);
+void import_site(Ctx& C, int k, int kind, int nblk, const int* meta, const double* data);
+void finalize_sites(Ctx& C);
+void build_envs(Ctx& C, int b);
+void setup_heff(Ctx& C, int b);
+void apply_heff_dev(Ctx& C, const double* in, double* out, int precision);
+void heff_diag(Ctx& C);
+int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);
+double truncate_step(Ctx& C, int dir, int Dmax);
+int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* st);
+
+// pack / unpack (serialisation)
+size_t pack_size(const OpSet& E);
+void pack_env(Ctx& C, const OpSet& E, unsigned char* dst, bool dst_device_or_pinned, cudaStream_t st);
+void unpack_env(Ctx& C, OpSet& E, const unsigned char* src, size_t bytes, bool src_device_or_pinned, cudaStream_t st);
+OpSet* env_of(Ctx& C, int side, int cut, bool create);
+
+}  // namespace gbd

@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/gbdmrg.h, validates arguments, and its host-side
+operator sets (Eq. 1 split at every cut, Sec. II.B) contract to the
+Jordan-Wigner matrix of Eq. 1."""
+import numpy as np
+import pytest
+
+import inputs
+import paper_2412_04676_gb300 as g
+from oracle import hamiltonian as H
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_04676_gb300 import build
+    build.build()
+
+
+def test_every_declared_symbol_is_exported():
+    names = g.declared_symbols()
+    assert len(names) >= 20
+    L = g.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert missing == []
+
+
+def test_argument_validation():
+    with pytest.raises(g.GbdError):
+        g.Context(3, 3, 0)   # odd N with even 2Sz
+    with pytest.raises(g.GbdError):
+        g.Context(3, 7, 1)   # too many electrons
+    c = g.Context(4, 4, 0)
+    h, eri = inputs.make_integrals(4, 3)
+    hb = h.copy()
+    hb[0, 1] += 1e-6
+    with pytest.raises(g.GbdError):
+        c.load_integrals(hb, eri)
+    eb = eri.copy()
+    eb[0, 1, 2, 3] += 1e-6
+    with pytest.raises(g.GbdError):
+        c.load_integrals(h, eb)
+
+
+@pytest.mark.parametrize("L,seed", [(2, 4), (3, 5), (4, 6), (5, 7)])
+def test_library_operator_sets_contract_to_eq1(L, seed):
+    h, eri = inputs.make_integrals(L, seed)
+    c = g.Context(L, L, L % 2)
+    c.load_integrals(h, eri)
+    Hd = c.mpo_dense()
+    Hj = H.jw_hamiltonian(h, eri).toarray()
+    assert np.abs(Hd - Hj).max() <= 1e-12 * max(1.0, np.abs(Hj).max())
+
+
+@pytest.mark.parametrize("switch", [2, 3, 4])
+def test_switch_position_does_not_change_hamiltonian(switch):
+    L = 5
+    h, eri = inputs.make_integrals(L, 21)
+    c = g.Context(L, 4, 0, switch_cut=switch)
+    c.load_integrals(h, eri)
+    assert np.abs(c.mpo_dense() - H.jw_hamiltonian(h, eri).toarray()).max() < 1e-12
+
+
+def test_bond_dimension_is_symmetric_and_quadratic():
+    L = 12
+    h, eri = inputs.make_integrals(L, 5)
+    c = g.Context(L, L, 0)
+    c.load_integrals(h, eri)
+    d = [c.mpo_bond_dim(k) for k in range(L + 1)]
+    assert d[0] == 1 and d[L] == 1
+    assert d == d[::-1]
+    assert max(d) == d[L // 2]
