@@ -368,7 +368,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 
 __global__ void pack_headers_kernel(unsigned char* __restrict__ base, const unsigned char* __restrict__ headers,
                                     const PackItem* __restrict__ items, int n) {
-    int i = blockIdx.x * 4 + (threadIdx.x >> 2);  // 4 threads x 16 bytes per header
+    int i = blockIdx.x * 64 + (threadIdx.x >> 2);  // 4 threads x 16 bytes per header, 64 headers per block
     if (i >= n) return;
     int part = threadIdx.x & 3;
     const uint4* src = reinterpret_cast<const uint4*>(headers + (size_t)i * 64) + part;
