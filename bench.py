@@ -1,0 +1,354 @@
+"""Benchmark of the two-site DMRG hot path on GB300 (one JSON line on stdout).
+
+Workload: L=30 orbitals, N=30 electrons, 2S_z=0, D=1024, seeded random
+integrals (stand-in for the FeMoco integrals), two-site position at the
+mid-chain cut (orbitals 14, 15).  One step = one full DMRG iteration of
+Sec. II.B: environments resident, enlargement of both blocks, Davidson with
+H_eff products to convergence, truncation to D, renormalisation, next start
+vector, and (offload on) the asynchronous pack of the new environment into
+pinned host RAM (Sec. III.A/B.4).  Steps alternate between the positions
+14 (moving right) and 15 (moving left), so every step rebuilds and saves one
+environment.
+
+metric: H_eff psi useful TFLOP/s = useful flops of the H_eff products in the
+timed steps (2*m*k*n over the non-zero sector GEMMs, counted once) divided
+by the device time of those steps (CUDA events on the library's compute
+stream).  e2e: the same steps through the public API with the two-site
+vector uploaded from pinned host memory before and read back after each
+step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "config2": dict(L=30, N=30, tsz=0, D=1024, seed=1002, b=14),
+    # a few-GB case of the same kernels, for profiler captures
+    "small": dict(L=16, N=16, tsz=0, D=512, seed=1002, b=7),
+}
+METRIC = "H_eff psi useful TFLOP/s (two-site DMRG step, L=30 N=30 D=1024 mid-chain)"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index=0):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        try:
+            sm = sorted(float(r[1]) for r in self.rows)
+            out["sm_mhz"] = sm[len(sm) // 2]
+            out["sm_max_mhz"] = max(float(r[2]) for r in self.rows)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = set()
+            for r in self.rows:
+                for i, nme in enumerate(names):
+                    if r[5 + i].lower() == "active":
+                        reasons.add(nme)
+            out["reasons"] = sorted(reasons)
+        except Exception:
+            pass
+        return out
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
+    """The oracle's H_eff psi on L=10, N=10, D=256 (mid-chain), timed on host cores.
+
+    Returns (useful TFLOP/s, cores, description, per-step seconds).
+    """
+    import numpy as np
+    from threadpoolctl import threadpool_info
+
+    import inputs
+    from oracle import dmrg as R
+    from oracle import hamiltonian as H
+    from oracle import mpo as M
+
+    L, N, tsz, D, b, seed = 10, 10, 0, 256, 4, 1001
+    h, eri = inputs.make_integrals(L, seed)
+    mp = M.MPO(L, H.hamiltonian_terms(h, eri))
+    sites, dims = inputs.make_mps(L, N, tsz, D, seed + 1, n_left=b)
+    EL = R.build_left_envs(sites, dims, mp, b)[b]
+    ER = R.build_right_envs(sites, dims, mp, b + 2, (N, tsz))[b + 2]
+    He = R.Heff(EL, ER, dims, mp, b)
+    flops = 0.0
+    for (Q, Q2), bl, br in He.pairs:
+        T, m1, m2 = bl.shape
+        n2 = He.shape[Q2][1]
+        n1 = He.shape[Q][1]
+        flops += 2.0 * T * m1 * m2 * n2 + 2.0 * T * m1 * n2 * n1
+    x = np.random.default_rng(0).normal(size=He.dim)
+    for _ in range(warmup):
+        He.matvec(x)
+    times = []
+    t0 = time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        He.matvec(x)
+        times.append(time.perf_counter() - t)
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() - t0 >= seconds:
+            break
+    cores = 0
+    try:
+        cores = max(int(x.get("num_threads", 0)) for x in threadpool_info())
+    except Exception:
+        cores = os.cpu_count() or 0
+    desc = (f"oracle H_eff psi at L=10,N=10,D=256 (config 1, mid-chain cut), dim {He.dim}, "
+            f"{len(times)} products in {sum(times):.1f} s; the oracle cannot build the L=30, D=1024 "
+            f"environments in bounded time")
+    return flops * len(times) / sum(times) / 1e12, cores, desc, times
+
+
+def _oracle_child(q, seconds):
+    try:
+        q.put(oracle_sample(seconds))
+    except Exception as e:  # reported, never fatal for the GPU arm
+        q.put(("error", repr(e)))
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cpu_t = []
+    value, cores, desc, times = oracle_sample(max_steps=args.steps, warmup=args.warmup)
+    ms = 1000.0 * sum(times) / len(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle sample: L=10 N=10 2Sz=0 D=256 mid-chain H_eff psi",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del cpu_t
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import multiprocessing as mp_
+
+    cpu_q = None
+    cpu_proc = None
+
+    import numpy as np
+    import torch
+
+    import inputs
+    import paper_2412_04676_gb300 as g
+    from paper_2412_04676_gb300 import build
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    W = WORKLOADS[args.workload]
+    L, N, tsz, D, b = W["L"], W["N"], W["tsz"], W["D"], W["b"]
+    prec = g.MIXED_BF16X3 if args.precision == "mixed" else g.FP64
+    h, eri = inputs.make_integrals(L, W["seed"])
+    sites, dims = inputs.make_mps(L, N, tsz, D, W["seed"] + 1 + rank, n_left=b)
+    ctx = g.Context(L, N, tsz, D=D, precision=prec, offload=not args.no_offload, device=local_rank,
+                    dav_tol=args.tol, dav_max_matvec=args.max_matvec)
+    ctx.load_integrals(h, eri)
+    ctx.import_mps(sites, [0] * b + [1] * (L - b))
+    ctx.build_envs(b)
+    secs, info = ctx.tables(b)
+    pos = [b]
+    dirs = [1]
+
+    def one_step():
+        p, d = pos[0], dirs[0]
+        st = ctx.step(p, d, D)
+        pos[0] = p + d
+        dirs[0] = -d
+        return st
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    l0 = g.launch_count()
+    stats = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        stats.append(one_step())
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    l1 = g.launch_count()
+    clk = clocks.stop()
+    barrier()
+    flops = sum(s["useful_flops"] for s in stats)
+    ms_dev = sum(s["ms_device"] for s in stats)
+    ms_mv = sum(s["ms_matvec"] for s in stats)
+    nmv = sum(s["matvecs"] for s in stats)
+    # end to end: the two-site vector crosses the host link every step
+    psi, pb = ctx.get_psi()
+    host = torch.from_numpy(psi).pin_memory()
+    e2e_ms = 0.0
+    e2e_flops = 0.0
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        ctx.set_psi(pos[0], host.numpy())
+        st = one_step()
+        out, pb = ctx.get_psi()
+        host = torch.from_numpy(out).pin_memory()
+        e2e_ms += 1000.0 * (time.perf_counter() - t)
+        e2e_flops += st["useful_flops"]
+        h2d += psi.nbytes
+        d2h += out.nbytes + 8
+        psi = out
+    # the oracle runs only after the GPU measurements, so it never competes for host cores
+    if rank == 0 and not args.no_cpu_baseline:
+        ctx_mp = mp_.get_context("spawn")
+        cpu_q = ctx_mp.Queue()
+        cpu_proc = ctx_mp.Process(target=_oracle_child, args=(cpu_q, args.cpu_seconds), daemon=True)
+        cpu_proc.start()
+    vals = torch.tensor([ms_dev, e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_dev_max, e2e_max = float(vals[0]), float(vals[1])
+    value = world * flops / (ms_dev_max * 1e-3) / 1e12
+    e2e_value = world * e2e_flops / (e2e_max * 1e-3) / 1e12
+    if rank != 0:
+        return 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    flops_mv = info["useful_flops"]
+    achieved = flops_mv / (ms_mv / nmv * 1e-3) / 1e12 if nmv else 0.0
+    if prec == g.FP64:
+        peak, bound, src = args.fp64_peak, "alu", "FP64 FMA pipe, derived (see DESIGN.md)"
+    else:
+        peak = peaks.get("bf16_tflops", 1900.0) / 3.0
+        bound, src = "tensor", "measured bf16 burst / 3 (BF16x3)"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "H_eff product (phase 1 + phase 2 launches)", "peak_source": src}
+    cpu = None
+    if cpu_q is not None:
+        try:
+            r = cpu_q.get(timeout=args.cpu_seconds + 240)
+            if r and r[0] != "error":
+                cpu = {"value": r[0], "unit": "TFLOP/s", "cores": r[1], "kind": "oracle", "sample": r[2]}
+            else:
+                cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": str(r)}
+        except Exception as e:
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": f"timeout {e!r}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_dev_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == g.FP64 else "bf16x3->f32",
+        "data": "synthetic",
+        "config": {"workload": (f"L={L} N={N} 2Sz={tsz} D={D} two-site step at the mid-chain cut"
+                                + (" (config 2)" if args.workload == "config2" else "")),
+                   "precision": args.precision, "offload": not args.no_offload,
+                   "environments": "renormalised on the GPU from a seeded random isometric MPS with the "
+                                   "D=1024 sector distribution",
+                   "l2": "operands larger than L2 (enlarged operators > 1 GB)",
+                   "parallelism": f"replicas x{world}", "psi_dim": info["dim"], "n_terms": info["n_terms"],
+                   "useful_gflop_per_product": flops_mv / 1e9},
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": int(l1 - l0),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "detail": {"matvec_tflops": achieved, "matvecs": nmv, "ms_matvec": ms_mv, "ms_device": ms_dev,
+                   "wall_s": t_wall, "energy": stats[-1]["energy"],
+                   "ms_io_exposed": sum(s["ms_io_exposed"] for s in stats),
+                   "bytes_packed_per_step": sum(s["bytes_packed"] for s in stats) / args.steps,
+                   "ms_truncate": sum(s["ms_truncate"] for s in stats),
+                   "ms_renorm": sum(s["ms_renorm"] for s in stats)},
+    }
+    print(json.dumps(line), flush=True)
+    if cpu_proc is not None:
+        cpu_proc.join(timeout=5)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
+    ap.add_argument("--no-offload", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-matvec", type=int, default=40)
+    ap.add_argument("--fp64-peak", type=float, default=1.25)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -121,6 +121,23 @@ typedef struct {
     double useful_flops;    /* H_eff useful flops over the sweep                 */
 } gbd_sweep_stats;
 
+typedef struct {
+    double energy;          /* Davidson energy (+ e_core)                        */
+    double trunc_weight;    /* discarded weight of the truncation                */
+    double resid;           /* final Davidson residual norm                      */
+    int matvecs;
+    double ms_total;        /* wall time of the step                             */
+    double ms_matvec;       /* device time of the H_eff products                 */
+    double ms_davidson;     /* Davidson excluding products                       */
+    double ms_truncate;     /* density matrices, eigensolves, renormalisation,
+                               next start vector                                */
+    double ms_renorm;       /* environment loads + enlargement (pre-processing)  */
+    double ms_io_exposed;   /* host waits on IO events                           */
+    double useful_flops;    /* H_eff useful flops of the step                    */
+    double bytes_packed;    /* environment bytes serialised to host this step    */
+    double ms_device;       /* CUDA-event span of the step on the compute stream */
+} gbd_step_stats;
+
 /* ---------------------------------------------------------------- lifecycle */
 int gbd_config_default(gbd_config* cfg);
 int gbd_create(const gbd_config* cfg, gbd_ctx** out);
@@ -191,6 +208,26 @@ int gbd_truncate(gbd_ctx* ctx, int b, int dir, int Dmax, double* trunc_weight);
  * from a seeded random one.  stats may be NULL; per-sweep stats are written
  * to stats[i] for i < nsweeps. */
 int gbd_sweep(gbd_ctx* ctx, int nsweeps, int D, gbd_sweep_stats* stats);
+
+/* One full two-site iteration at position b (Sec. II.B): environments made
+ * resident (unpacked from host if offloaded), enlargement, Davidson from the
+ * current two-site vector (random if none), truncation to D towards dir
+ * (+1 right, -1 left), renormalisation, next start vector; with offload on,
+ * the next needed environment is loaded and the new one saved to pinned host
+ * memory asynchronously (Sec. III.B.4).  The position moves to b + dir. */
+int gbd_step(gbd_ctx* ctx, int b, int dir, int D, gbd_step_stats* stats);
+
+/* Copies the current two-site vector (position *b, sector-major layout) to
+ * host memory.  *n gets its length; cap too small -> GBD_ERR_ARG. */
+int gbd_get_psi(gbd_ctx* ctx, double* out, size_t cap, long long* n, int* b);
+
+/* Sets the current two-site vector at position b from psi (n doubles,
+ * sector-major layout of position b; host or device memory, flagged).  The
+ * environments of position b must exist.  Wrong n -> GBD_ERR_ARG. */
+int gbd_set_psi(gbd_ctx* ctx, int b, const double* psi, long long n, int on_device);
+
+/* Number of this library's own kernel launches so far (all contexts). */
+int gbd_launch_count(unsigned long long* count);
 
 /* Current energies of the last sweep steps, one per step (host array). */
 int gbd_step_energies(gbd_ctx* ctx, double* out, int cap, int* n);

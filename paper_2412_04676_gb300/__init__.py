@@ -45,6 +45,13 @@ class HeffInfo(C.Structure):
                 ("n_gemm", C.c_longlong), ("useful_flops", C.c_double), ("operator_bytes", C.c_double)]
 
 
+class StepStats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("trunc_weight", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int),
+                ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("ms_davidson", C.c_double),
+                ("ms_truncate", C.c_double), ("ms_renorm", C.c_double), ("ms_io_exposed", C.c_double),
+                ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double)]
+
+
 class DavStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int), ("iterations", C.c_int),
                 ("ms_matvec", C.c_double)]
@@ -82,6 +89,10 @@ _SIGS = {
     "gbd_truncate": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "gbd_sweep": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "gbd_step_energies": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
+    "gbd_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(StepStats)]),
+    "gbd_get_psi": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "gbd_launch_count": (C.c_int, [C.POINTER(C.c_ulonglong)]),
+    "gbd_set_psi": (C.c_int, [_P, C.c_int, _P, C.c_longlong, C.c_int]),
     "gbd_pack_env": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t), C.c_int]),
     "gbd_unpack_env": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.c_int]),
     "gbd_env_import": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P]),
@@ -89,6 +100,12 @@ _SIGS = {
     "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
 }
+
+
+def launch_count():
+    v = C.c_ulonglong()
+    _check(lib().gbd_launch_count(C.byref(v)))
+    return v.value
 
 
 def declared_symbols():
@@ -234,6 +251,24 @@ class Context:
         st = (SweepStats * nsweeps)()
         _check(lib().gbd_sweep(self.h, nsweeps, D, C.cast(st, C.c_void_p)))
         return [s.as_dict() for s in st]
+
+    def step(self, b, direction, D):
+        st = StepStats()
+        _check(lib().gbd_step(self.h, b, direction, D, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in StepStats._fields_}
+
+    def get_psi(self, out=None):
+        n = C.c_longlong()
+        b = C.c_int()
+        _check(lib().gbd_get_psi(self.h, None, 0, C.byref(n), C.byref(b)))
+        if out is None:
+            out = np.zeros(n.value)
+        _check(lib().gbd_get_psi(self.h, _ptr(out), out.size, C.byref(n), C.byref(b)))
+        return out, b.value
+
+    def set_psi(self, b, psi):
+        n = psi.numel() if hasattr(psi, "numel") else psi.size
+        _check(lib().gbd_set_psi(self.h, b, _ptr(psi), n, _on_device(psi)))
 
     def step_energies(self):
         n = C.c_int()

@@ -226,6 +226,64 @@ int gbd_sweep(gbd_ctx* c, int nsweeps, int D, gbd_sweep_stats* stats) {
     });
 }
 
+int gbd_step(gbd_ctx* c, int b, int dir, int D, gbd_step_stats* stats) {
+    return guard([&] {
+        GBD_REQUIRE(dir == 1 || dir == -1, GBD_ERR_ARG, "dir must be +1 or -1");
+        GBD_REQUIRE(D >= 1, GBD_ERR_ARG, "D must be >= 1");
+        run_step(ctx(c), b, dir, D, stats);
+        return GBD_OK;
+    });
+}
+
+int gbd_get_psi(gbd_ctx* c, double* out, size_t cap, long long* n, int* b) {
+    return guard([&] {
+        Ctx& C = ctx(c);
+        GBD_REQUIRE(C.psi_valid, GBD_ERR_STATE, "no two-site vector");
+        size_t len = C.psi.bytes / sizeof(double);
+        // the vector length is that of the layout at psi_b
+        if (C.H.b == C.psi_b) len = size_t(C.H.dim);
+        else {
+            const Bond& bl = C.bonds[C.psi_b];
+            const Bond& br = C.bonds[C.psi_b + 2];
+            EBasis eL = left_enlarged(bl), eR = right_enlarged(br);
+            len = 0;
+            for (size_t i = 0; i < eL.q.size(); ++i) {
+                int j = eR.find(eL.q[i]);
+                if (j >= 0) len += size_t(eL.dim[i]) * eR.dim[j];
+            }
+        }
+        if (n) *n = (long long)len;
+        if (b) *b = C.psi_b;
+        if (out) {
+            GBD_REQUIRE(cap >= len, GBD_ERR_ARG, "output too small");
+            GBD_CHECK_CUDA(cudaMemcpy(out, C.psi.p, len * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        return GBD_OK;
+    });
+}
+
+int gbd_set_psi(gbd_ctx* c, int b, const double* psi, long long n, int on_device) {
+    return guard([&] {
+        Ctx& C = ctx(c);
+        GBD_REQUIRE(psi, GBD_ERR_ARG, "null vector");
+        ensure_heff(C, b);
+        GBD_REQUIRE(n == C.H.dim, GBD_ERR_ARG, "vector length does not match the layout at b");
+        C.psi.ensure(size_t(n) * sizeof(double));
+        GBD_CHECK_CUDA(cudaMemcpyAsync(C.psi.p, psi, size_t(n) * sizeof(double),
+                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, C.cs));
+        GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+        C.psi_valid = true;
+        C.psi_b = b;
+        return GBD_OK;
+    });
+}
+
+int gbd_launch_count(unsigned long long* count) {
+    if (!count) { g_err = "null output"; return GBD_ERR_ARG; }
+    *count = launch_count();
+    return GBD_OK;
+}
+
 int gbd_step_energies(gbd_ctx* c, double* out, int cap, int* n) {
     return guard([&] {
         Ctx& C = ctx(c);

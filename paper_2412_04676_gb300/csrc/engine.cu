@@ -1109,6 +1109,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         long long nel = (long long)m[si] * k;
         gather_eigvec_kernel<<<unsigned(std::min<long long>((nel + 255) / 256, 4096)), 256, 0, s>>>(
             rho.as<double>() + roff[si], m[si], k, I.data.as<double>() + I.off[i]);
+        count_launch();
         int mL = H.bL.dim[H.sL[si]], mR = H.bR.dim[H.sR[si]];
         GemmTask t{};
         t.C = Cbuf.as<double>() + coff[i];
@@ -1264,6 +1265,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     }
     GBD_CHECK_CUDA(cudaStreamSynchronize(s));
     (void)L;
+    C.H = Heff();  // the enlarged operators belong to the old position
     return weight;
 }
 

@@ -113,6 +113,7 @@ void heff_diag(Ctx& C);
 int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);
 double truncate_step(Ctx& C, int dir, int Dmax);
 int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* st);
+void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* st);
 
 // pack / unpack (serialisation)
 size_t pack_size(const OpSet& E);

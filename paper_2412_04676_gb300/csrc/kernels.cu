@@ -16,7 +16,13 @@
 #include "core.h"
 #include "kernels.h"
 
+#include <atomic>
+
 namespace gbd {
+
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(); }
+void count_launch(unsigned n) { g_launches += n; }
 
 // ============================================================== grouped GEMM
 namespace {
@@ -183,6 +189,7 @@ void GemmPlan::launch(cudaStream_t st) const {
     GBD_REQUIRE(n <= maxgrid, GBD_ERR_ARG, "too many GEMM tiles");
     gemm_f64_kernel<<<unsigned(n), NT, 0, st>>>((const GemmTask*)d_tasks, (const GemmSeg*)d_segs,
                                                 (const GemmTile*)d_tiles);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -283,6 +290,7 @@ void multi_dot(const double* V, long long ldv, int k, const double* x, long long
     GBD_REQUIRE(k >= 1 && k <= MAXK, GBD_ERR_ARG, "multi_dot: k out of range");
     multi_dot_partial_kernel<<<DOT_BLOCKS, VT, 0, st>>>(V, ldv, k, x, n, partial);
     multi_dot_final_kernel<<<1, 64, 0, st>>>(partial, DOT_BLOCKS, k, out);
+    count_launch(2);
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -290,27 +298,32 @@ void combine(const double* V, long long ldv, int k, const double* c, double* y, 
              double beta, cudaStream_t st) {
     GBD_REQUIRE(k >= 1 && k <= MAXK, GBD_ERR_ARG, "combine: k out of range");
     combine_kernel<<<grid_for(n), VT, 0, st>>>(V, ldv, k, c, y, n, alpha, beta);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
 void precondition(const double* r, const double* diag, double theta, double* t, long long n, cudaStream_t st) {
     precond_kernel<<<grid_for(n), VT, 0, st>>>(r, diag, theta, t, n);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
 void axpby(const double* x, double* y, long long n, double a, double b, cudaStream_t st) {
     axpby_kernel<<<grid_for(n), VT, 0, st>>>(x, y, n, a, b);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
 void scale(double* x, long long n, double a, cudaStream_t st) {
     scale_kernel<<<grid_for(n), VT, 0, st>>>(x, n, a);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
 void fill_zero(double* p, long long n, cudaStream_t st) {
     if (n <= 0) return;
     zero_kernel<<<grid_for(n), VT, 0, st>>>(p, n);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -345,6 +358,7 @@ void heff_diagonal(const std::vector<DiagTask>& tasks, const std::vector<DiagSeg
     GBD_REQUIRE(tasks.size() < 65536, GBD_ERR_ARG, "too many diagonal tasks");
     dim3 grid(64, unsigned(tasks.size()));
     diag_kernel<<<grid, 256, 0, st>>>(dt, ds);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
     GBD_CHECK_CUDA(cudaFreeAsync(dt, st));
     GBD_CHECK_CUDA(cudaFreeAsync(ds, st));
@@ -427,15 +441,16 @@ void pack_launch(unsigned char* base, const unsigned char* d_headers, const Pack
                  const PackChunk* d_chunks, int n_chunks, unsigned long long* d_cks, cudaStream_t st) {
     if (n_items == 0) return;
     GBD_CHECK_CUDA(cudaMemsetAsync(d_cks, 0, sizeof(unsigned long long) * n_items, st));
-    if (d_headers) pack_headers_kernel<<<(n_items + 63) / 64, 256, 0, st>>>(base, d_headers, d_items, n_items);
-    if (n_chunks > 0) pack_payload_kernel<<<n_chunks, PT, 0, st>>>(base, d_items, d_chunks, d_cks);
+    if (d_headers) { pack_headers_kernel<<<(n_items + 63) / 64, 256, 0, st>>>(base, d_headers, d_items, n_items); count_launch(); }
+    if (n_chunks > 0) { pack_payload_kernel<<<n_chunks, PT, 0, st>>>(base, d_items, d_chunks, d_cks); count_launch(); }
     pack_checksums_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(base, d_items, d_cks, n_items);
+    count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
 void unpack_launch(const unsigned char* base, const PackItem* d_items, const PackChunk* d_chunks, int n_chunks,
                    unsigned long long* d_cks, cudaStream_t st) {
-    if (n_chunks > 0) unpack_payload_kernel<<<n_chunks, PT, 0, st>>>(base, d_items, d_chunks, d_cks);
+    if (n_chunks > 0) { unpack_payload_kernel<<<n_chunks, PT, 0, st>>>(base, d_items, d_chunks, d_cks); count_launch(); }
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 

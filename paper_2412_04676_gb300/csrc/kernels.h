@@ -108,6 +108,9 @@ void unpack_launch(const unsigned char* stream_base, const PackItem* d_items, co
                    int n_chunks, unsigned long long* d_cks, cudaStream_t st);
 
 // ------------------------------------------------------------------ misc
+// Count of this library's kernel launches (incremented by every launcher).
+unsigned long long launch_count();
+void count_launch(unsigned n = 1);
 void fill_zero(double* p, long long n, cudaStream_t st);
 
 }  // namespace gbd

@@ -409,7 +409,73 @@ void ensure_resident(Ctx& C, int side, int cut) {
 
 }  // namespace
 
-// ============================================================== sweep
+// ============================================================== step / sweep
+// One DMRG iteration of Sec. II.B at position b, moving towards dir.
+void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
+    GBD_REQUIRE(C.have_ints, GBD_ERR_STATE, "load integrals first");
+    GBD_REQUIRE(b >= 0 && b + 1 < C.L, GBD_ERR_ARG, "two-site position out of range");
+    ensure_cuda(C);
+    const bool off = C.cfg.offload != 0;
+    const int L = C.L;
+    double t0 = now_ms();
+    double io0 = C.io_exposed_ms, d2h0 = C.io_d2h, mv0 = C.ms_matvec_acc;
+    cudaEvent_t ea, eb;
+    GBD_CHECK_CUDA(cudaEventCreate(&ea));
+    GBD_CHECK_CUDA(cudaEventCreate(&eb));
+    GBD_CHECK_CUDA(cudaEventRecord(ea, C.cs));
+    // pre-processing: environments resident, enlarged operators
+    ensure_resident(C, 0, b);
+    ensure_resident(C, 1, b + 2);
+    if (C.H.b != b || !C.H.OL.resident()) setup_heff(C, b);
+    if (off) {  // both environments are consumed by the enlargement
+        release_async(C, 0, b);
+        release_async(C, 1, b + 2);
+    }
+    double t1 = now_ms();
+    double e = 0.0;
+    gbd_dav_stats ds{};
+    davidson(C, nullptr, &e, &ds);
+    double flops = C.H.flops * ds.matvecs;
+    double t2 = now_ms();
+    double w = truncate_step(C, dir, D);
+    if (off) {
+        // Sec. III.B.4: the next environment is loaded right after the
+        // renormalisation, then the new one is saved asynchronously
+        int nb = b + dir;
+        if (nb >= 0 && nb + 1 < L) {
+            int need_side = dir == 1 ? 1 : 0;
+            int need_cut = dir == 1 ? nb + 2 : nb;
+            OpSet* nE = env_of(C, need_side, need_cut, false);
+            if (nE && !nE->resident()) load_async(C, need_side, need_cut);
+        }
+        if (dir == 1) save_async(C, 0, b + 1);
+        else save_async(C, 1, b + 1);
+    }
+    GBD_CHECK_CUDA(cudaEventRecord(eb, C.cs));
+    GBD_CHECK_CUDA(cudaEventSynchronize(eb));
+    float msd = 0.f;
+    cudaEventElapsedTime(&msd, ea, eb);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    double t3 = now_ms();
+    C.step_energy.push_back(e);
+    if (out) {
+        out->ms_device = msd;
+        out->energy = e;
+        out->trunc_weight = w;
+        out->resid = ds.resid;
+        out->matvecs = ds.matvecs;
+        out->ms_total = t3 - t0;
+        out->ms_matvec = C.ms_matvec_acc - mv0;
+        out->ms_davidson = (t2 - t1) - out->ms_matvec;
+        out->ms_truncate = t3 - t2;
+        out->ms_renorm = t1 - t0;
+        out->ms_io_exposed = C.io_exposed_ms - io0;
+        out->useful_flops = flops;
+        out->bytes_packed = C.io_d2h - d2h0;
+    }
+}
+
 int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* stats) {
     GBD_REQUIRE(C.have_ints, GBD_ERR_STATE, "load integrals first");
     const int L = C.L;
@@ -447,7 +513,6 @@ int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* stats) {
                     const Seg* g1 = nullptr;
                     for (const auto& g : B1.basis.segs[e1]) if (g.s == sr.s) g1 = &g;
                     if (!g1) continue;
-                    // B0 row (1 x d1): V0[(g0->off + a)][0], a < d1 ; B1 (d1 x size): V1[(g1->off + j)][a]
                     for (int j = 0; j < g1->size; ++j) {
                         double v = 0.0;
                         for (int a = 0; a < d1; ++a)
@@ -467,60 +532,27 @@ int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* stats) {
         gbd_sweep_stats st{};
         st.energy_min = 1e300;
         double t_start = now_ms();
-        double mv0 = C.ms_matvec_acc, io0 = C.io_exposed_ms, pk0 = C.pack_ms, d2h0 = C.io_d2h;
-        int mvc0 = C.matvec_count;
-        double flops = 0.0, t_dav = 0.0, t_tr = 0.0, t_ren = 0.0;
+        double pk0 = C.pack_ms;
         auto step = [&](int b, int dir) {
-            double t0 = now_ms();
-            ensure_resident(C, 0, b);
-            ensure_resident(C, 1, b + 2);
-            if (C.H.b != b || !C.H.OL.resident()) setup_heff(C, b);
-            if (off) {  // both environments are consumed by the enlargement
-                release_async(C, 0, b);
-                release_async(C, 1, b + 2);
-            }
-            double t1 = now_ms();
-            double e = 0.0;
-            gbd_dav_stats ds{};
-            int rc = davidson(C, nullptr, &e, &ds);
-            (void)rc;
-            double t2 = now_ms();
-            flops += C.H.flops * ds.matvecs;
-            double w = truncate_step(C, dir, D);
-            double t3 = now_ms();
-            st.max_trunc = std::max(st.max_trunc, w);
-            st.matvecs += ds.matvecs;
-            st.energy_last = e;
-            st.energy_min = std::min(st.energy_min, e);
-            C.step_energy.push_back(e);
-            if (off) {
-                // Sec. III.B.4: the next environment is loaded right after the
-                // renormalisation, then the new one is saved asynchronously
-                int nb = b + dir;
-                int need_side = dir == 1 ? 1 : 0;
-                int need_cut = dir == 1 ? nb + 2 : nb;
-                OpSet* nE = env_of(C, need_side, need_cut, false);
-                if (nE && !nE->resident() && nb >= 0 && nb + 1 < L) load_async(C, need_side, need_cut);
-                if (dir == 1) save_async(C, 0, b + 1);
-                else save_async(C, 1, b + 1);
-            }
-            t_ren += (t1 - t0);
-            t_dav += (t2 - t1);
-            t_tr += (t3 - t2);
+            gbd_step_stats ss{};
+            run_step(C, b, dir, D, &ss);
+            st.max_trunc = std::max(st.max_trunc, ss.trunc_weight);
+            st.matvecs += ss.matvecs;
+            st.energy_last = ss.energy;
+            st.energy_min = std::min(st.energy_min, ss.energy);
+            st.ms_matvec += ss.ms_matvec;
+            st.ms_davidson += ss.ms_davidson;
+            st.ms_truncate += ss.ms_truncate;
+            st.ms_renorm += ss.ms_renorm;
+            st.ms_io_exposed += ss.ms_io_exposed;
+            st.bytes_packed += ss.bytes_packed;
+            st.useful_flops += ss.useful_flops;
         };
         for (int b = 0; b <= L - 3; ++b) step(b, 1);
         for (int b = L - 2; b >= 1; --b) step(b, -1);
         GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
         st.ms_total = now_ms() - t_start;
-        st.ms_matvec = C.ms_matvec_acc - mv0;
-        st.ms_davidson = t_dav - st.ms_matvec;
-        st.ms_truncate = t_tr;
-        st.ms_renorm = t_ren;
-        st.ms_io_exposed = C.io_exposed_ms - io0;
         st.ms_pack = C.pack_ms - pk0;
-        st.bytes_packed = C.io_d2h - d2h0;
-        st.useful_flops = flops;
-        (void)mvc0;
         if (stats) stats[sw] = st;
     }
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.ios));
