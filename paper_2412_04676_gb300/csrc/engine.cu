@@ -682,8 +682,6 @@ void setup_heff(Ctx& C, int b) {
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
 }
 
-void tc_prepare(Ctx& C);
-void tc_apply(Ctx& C);
 
 void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     Heff& H = C.H;
@@ -699,6 +697,10 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     GBD_CHECK_CUDA(cudaEventRecord(C.ev1, C.cs));
     GBD_CHECK_CUDA(cudaMemcpyAsync(out, H.yout.p, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventSynchronize(C.ev1));
+    if (precision == GBD_MIXED_BF16X3) {
+        int e = tc_error(C);
+        GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core product stopped on a bounded wait (code " + std::to_string(e) + ")");
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, C.ev0, C.ev1);
     C.ms_matvec_acc += ms;

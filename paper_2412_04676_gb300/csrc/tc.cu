@@ -1,16 +1,650 @@
-// tc.cu -- mixed-precision H_eff products (BF16x3 split, FP32 accumulate).
+// tc.cu -- mixed-precision H_eff products on the GB300 tensor cores.
+//
+// The product of Sec. II.B step 2 is two grouped GEMM phases over the
+// symmetry sectors (X = O^Lx_stacked psi, then Y += sum_t X_t (O^xR_t)^T with
+// one long K over layers t and inner index j).  Here every operand is split
+// once into BF16 hi + lo (x = hi + lo + O(2^-18 x)) and each tile computes
+// A_hi B_hi + A_hi B_lo + A_lo B_hi with tcgen05.mma (kind::f16, FP32
+// accumulation in TMEM).  The accumulator is promoted to FP64 registers
+// every `promote` K chunks through two ping-pong TMEM buffers, so the long
+// phase-2 reductions do not accumulate FP32 rounding.  Operands reach shared
+// memory through TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
+// three-stage mbarrier pipeline; one thread issues TMA, one issues MMA, eight
+// warps drain TMEM.  Zero fill of TMA boxes handles ragged sector edges.
+// Every spin-wait is bounded: on expiry the CTA records an error code in a
+// device word, stops issuing, waits (bounded) for its copies and frees TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
 #include "engine.h"
+#include "tc.h"
 
 namespace gbd {
+namespace tc {
 
-void tc_prepare(Ctx& C) {
-    (void)C;
-    throw Error(GBD_ERR_ARG, "mixed-precision products are not available in this build");
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kSpinCycles) return false;
+    }
+    return true;
 }
 
+__device__ __forceinline__ void tma_2d(uint32_t dst, const void* map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const void* map, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= uint64_t((addr >> 4) & 0x3FFF);
+    d |= uint64_t(1) << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;     // stride byte offset
+    d |= uint64_t(1) << 46;             // descriptor version
+    d |= uint64_t(2) << 61;             // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// position (segment, layer, inner offset) of global chunk c
+__device__ __forceinline__ void locate(const KSeg* segs, int seg0, int nseg, int c, int& s, int& t, int& j0) {
+    s = seg0;
+    while (s < seg0 + nseg && c >= segs[s].nchunk) { c -= segs[s].nchunk; ++s; }
+    if (s >= seg0 + nseg) { t = 0; j0 = 0; return; }
+    int kch = (segs[s].K + BK - 1) / BK;
+    t = c / kch;
+    j0 = (c % kch) * BK;
+}
+
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restrict__ works, const KSeg* __restrict__ segs,
+                                                             const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const Work w = works[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = w.c1 - w.c0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), 8);
+        }
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const int promote = w.promote > 0 ? w.promote : (1 << 30);
+    const int ndrain = n > 0 ? (n + promote - 1) / promote : 0;
+
+    if (warp == 0 && lane == 0 && n > 0) {
+        // ---------------- TMA producer
+        int s, t, j0;
+        locate(segs, w.seg0, w.nseg, w.c0, s, t, j0);
+        int issued = 0;
+        for (int i = 0; i < n; ++i) {
+            const int st = i % STAGES;
+            if (i >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), ((i / STAGES) & 1) ^ 1)) {
+                atomicExch(err, 1);
+                abort_s = 1;
+                break;
+            }
+            if (abort_s) break;
+            const KSeg sg = segs[s];
+            const uint32_t bar = smem_u32(&full_bar[st]);
+            uint8_t* base = smem + st * STAGE_BYTES;
+            mbar_expect_tx(bar, STAGE_BYTES);
+            const CUtensorMap* mA = maps + sg.mapA;
+            const CUtensorMap* mB = maps + sg.mapB;
+            if (sg.rank == 3) {
+                tma_3d(smem_u32(base), mA, j0, sg.a_row + w.m0, t, bar);
+                tma_3d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, t, bar);
+                tma_3d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, t, bar);
+                tma_3d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, t, bar);
+            } else {
+                tma_2d(smem_u32(base), mA, j0, sg.a_row + w.m0, bar);
+                tma_2d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, bar);
+                tma_2d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, bar);
+                tma_2d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, bar);
+            }
+            ++issued;
+            j0 += BK;
+            if (j0 >= sg.K) {
+                j0 = 0;
+                if (++t >= sg.T) { t = 0; ++s; }
+            }
+        }
+        // on abort: let the loads already issued land before the CTA may exit
+        for (int i = (issued > STAGES ? issued - STAGES : 0); abort_s && i < issued; ++i)
+            mbar_wait(smem_u32(&full_bar[i % STAGES]), (i / STAGES) & 1);
+    } else if (warp == 1 && lane == 0 && n > 0) {
+        // ---------------- MMA issuer
+        int buf = 0, inbuf = 0;
+        int fill0 = 0, fill1 = 0;  // completed fills of each accumulator buffer
+        for (int i = 0; i < n; ++i) {
+            const int st = i % STAGES;
+            if (!mbar_wait(smem_u32(&full_bar[st]), (i / STAGES) & 1)) {
+                atomicExch(err, 2);
+                abort_s = 1;
+                break;
+            }
+            if (abort_s) break;
+            tc_fence_after();
+            const int fills = buf ? fill1 : fill0;
+            if (inbuf == 0 && fills > 0) {
+                if (!mbar_wait(smem_u32(&tempty[buf]), (fills - 1) & 1)) {
+                    atomicExch(err, 3);
+                    abort_s = 1;
+                    break;
+                }
+                tc_fence_after();
+            }
+            const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t a_lo = a_hi + A_BYTES;
+            const uint32_t b_hi = a_hi + 2 * A_BYTES;
+            const uint32_t b_lo = b_hi + B_BYTES;
+            const uint32_t d = tmem + uint32_t(buf * BN);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+                const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
+                const uint64_t dah = sdesc(a_hi + off), dal = sdesc(a_lo + off);
+                const uint64_t dbh = sdesc(b_hi + off), dbl = sdesc(b_lo + off);
+                umma(d, dah, dbh, (inbuf > 0 || k > 0) ? 1u : 0u);
+                umma(d, dah, dbl, 1u);
+                umma(d, dal, dbh, 1u);
+            }
+            umma_commit(smem_u32(&empty_bar[st]));
+            ++inbuf;
+            if (inbuf == promote || i == n - 1) {
+                umma_commit(smem_u32(&tfull[buf]));
+                if (buf) ++fill1; else ++fill0;
+                buf ^= 1;
+                inbuf = 0;
+            }
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> FP64 registers
+        const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;   // column half
+        const int row = quad * 32 + lane;
+        double acc[BN / 2];
+#pragma unroll
+        for (int i = 0; i < BN / 2; ++i) acc[i] = 0.0;
+        for (int dd = 0; dd < ndrain; ++dd) {
+            const int buf = dd & 1;
+            bool ok = mbar_wait(smem_u32(&tfull[buf]), (dd >> 1) & 1);
+            if (!ok) { atomicExch(err, 4); abort_s = 1; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + half * (BN / 2) + c * 32);
+                tmem_ld32(taddr, r);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[c * 32 + i] += double(__uint_as_float(r[i]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+        }
+        const int gr = w.m0 + row;
+        const int gc0 = w.n0 + half * (BN / 2);
+        if (w.out_kind == 0) {
+            double* out = reinterpret_cast<double*>(w.out_hi) + (long long)row * BN + half * (BN / 2);
+#pragma unroll
+            for (int i = 0; i < BN / 2; i += 2) *reinterpret_cast<double2*>(out + i) = make_double2(acc[i], acc[i + 1]);
+        } else if (w.out_kind == 1) {
+            if (gr < w.M) {
+                __nv_bfloat16* oh = reinterpret_cast<__nv_bfloat16*>(w.out_hi) + (long long)gr * w.ldo;
+                __nv_bfloat16* ol = reinterpret_cast<__nv_bfloat16*>(w.out_lo) + (long long)gr * w.ldo;
+#pragma unroll
+                for (int i = 0; i < BN / 2; ++i) {
+                    const int gc = gc0 + i;
+                    if (gc < w.N) {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(float(acc[i]));
+                        oh[gc] = h;
+                        ol[gc] = __float2bfloat16_rn(float(acc[i] - double(__bfloat162float(h))));
+                    }
+                }
+            }
+        } else {
+            if (gr < w.M) {
+                double* o = reinterpret_cast<double*>(w.out_hi) + (long long)gr * w.ldo;
+#pragma unroll
+                for (int i = 0; i < BN / 2; ++i)
+                    if (gc0 + i < w.N) o[gc0 + i] = acc[i];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi); rows padded with zeros
+struct SplitBlock {
+    const double* src;
+    __nv_bfloat16* hi;
+    __nv_bfloat16* lo;
+    long long rows;
+    int cols, ldd;
+};
+
+__global__ void split_kernel(const SplitBlock* __restrict__ blocks, int nb) {
+    const SplitBlock b = blocks[blockIdx.y];
+    const long long n = b.rows * b.ldd;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / b.ldd;
+        const int c = int(e % b.ldd);
+        double x = c < b.cols ? b.src[r * b.cols + c] : 0.0;
+        __nv_bfloat16 h = __float2bfloat16_rn(float(x));
+        b.hi[e] = h;
+        b.lo[e] = __float2bfloat16_rn(float(x - double(__bfloat162float(h))));
+    }
+}
+
+// psi^T per sector: dst[n][k] = psi[k][n], split into hi / lo
+__global__ void split_psi_kernel(const double* __restrict__ psi, const TcHeff::PsiSec* __restrict__ secs,
+                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+    const TcHeff::PsiSec s = secs[blockIdx.y];
+    const long long n = (long long)s.mR * s.ldp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int r = int(e / s.ldp);  // column of psi
+        const int k = int(e % s.ldp);  // row of psi
+        double x = k < s.mL ? psi[s.src + (long long)k * s.mR + r] : 0.0;
+        __nv_bfloat16 h = __float2bfloat16_rn(float(x));
+        hi[s.dst + e] = h;
+        lo[s.dst + e] = __float2bfloat16_rn(float(x - double(__bfloat162float(h))));
+    }
+}
+
+__global__ void reduce_kernel(const Reduce* __restrict__ red, const double* __restrict__ partial) {
+    const Reduce r = red[blockIdx.x];
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+        const int i = e / BN, j = e % BN;
+        const int gi = r.m0 + i, gj = r.n0 + j;
+        if (gi >= r.M || gj >= r.N) continue;
+        double v = 0.0;
+        for (int p = r.p0; p < r.p1; ++p) v += partial[(long long)p * BM * BN + e];
+        r.out[(long long)gi * r.ldo + gj] = v;
+    }
+}
+
+__global__ void zero_rows_kernel(const Reduce* __restrict__ red) {
+    const Reduce r = red[blockIdx.x];
+    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
+        const int gi = r.m0 + e / BN, gj = r.n0 + e % BN;
+        if (gi < r.M && gj < r.N) r.out[(long long)gi * r.ldo + gj] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        GBD_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        GBD_REQUIRE(p && q == cudaDriverEntryPointSuccess, GBD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// BF16 K-major operand: inner extent K (elements), rows, optional layers; row
+// pitch ld elements (multiple of 8), layer pitch in elements.
+CUtensorMap make_map(const void* base, int K, long long rows, int layers, int ld, long long layer_pitch, int box_rows) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    GBD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && ld % 8 == 0, GBD_ERR_STATE, "TMA operand misaligned");
+    cuuint64_t dims[3] = {cuuint64_t(std::max(K, 1)), cuuint64_t(std::max<long long>(rows, 1)), cuuint64_t(std::max(layers, 1))};
+    cuuint64_t strides[2] = {cuuint64_t(ld) * 2, cuuint64_t(layer_pitch) * 2};
+    cuuint32_t box[3] = {cuuint32_t(BK), cuuint32_t(box_rows), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint32_t rank = layers > 0 ? 3 : 2;
+    CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GBD_REQUIRE(r == CUDA_SUCCESS, GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+inline int pad8(int x) { return (x + 7) / 8 * 8; }
+
+}  // namespace tc
+
+using namespace tc;
+
+// Builds BF16 operands, tensor maps and work lists for the current position.
+void tc_prepare(Ctx& C) {
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    T = TcHeff();
+    cudaStream_t st = C.cs;
+    // ---- BF16 operator arenas (hi / lo), rows padded to 8 elements
+    auto layout = [&](const OpSet& O, std::vector<std::vector<long long>>& off) {
+        long long tot = 0;
+        off.assign(O.cls.size(), {});
+        for (size_t c = 0; c < O.cls.size(); ++c)
+            for (const auto& b : O.cls[c].blocks) {
+                off[c].push_back(tot);
+                tot += (long long)O.cls[c].states.size() * b.rows * pad8(b.cols);
+            }
+        return tot;
+    };
+    std::vector<std::vector<long long>> offL, offR;
+    long long nL = layout(H.OL, offL), nR = layout(H.OR, offR);
+    T.ol_hi.ensure(size_t(std::max(nL, 8LL)) * 2);
+    T.ol_lo.ensure(size_t(std::max(nL, 8LL)) * 2);
+    T.or_hi.ensure(size_t(std::max(nR, 8LL)) * 2);
+    T.or_lo.ensure(size_t(std::max(nR, 8LL)) * 2);
+    T.bytes_ops = double(nL + nR) * 4.0;
+    std::vector<SplitBlock> sb;
+    auto add_split = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& hi, DevBuf& lo) {
+        for (size_t c = 0; c < O.cls.size(); ++c)
+            for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
+                const OpBlock& b = O.cls[c].blocks[i];
+                sb.push_back({O.data.as<double>() + b.off, hi.as<__nv_bfloat16>() + off[c][i],
+                              lo.as<__nv_bfloat16>() + off[c][i], (long long)O.cls[c].states.size() * b.rows, b.cols,
+                              pad8(b.cols)});
+            }
+    };
+    add_split(H.OL, offL, T.ol_hi, T.ol_lo);
+    add_split(H.OR, offR, T.or_hi, T.or_lo);
+    if (!sb.empty()) {
+        DevBuf d;
+        d.ensure(sb.size() * sizeof(SplitBlock));
+        GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, sb.data(), sb.size() * sizeof(SplitBlock), cudaMemcpyHostToDevice, st));
+        for (size_t i0 = 0; i0 < sb.size(); i0 += 65535) {
+            unsigned nb = unsigned(std::min<size_t>(65535, sb.size() - i0));
+            split_kernel<<<dim3(32, nb), 256, 0, st>>>(d.as<SplitBlock>() + i0, int(nb));
+            count_launch();
+        }
+        GBD_CHECK_CUDA(cudaGetLastError());
+        GBD_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- psi^T sectors
+    long long np = 0;
+    for (size_t s = 0; s < H.sq.size(); ++s) {
+        int mL = H.bL.dim[H.sL[s]], mR = H.bR.dim[H.sR[s]];
+        T.psec.push_back({H.soff[s], np, mL, mR, pad8(mL)});
+        np += (long long)mR * pad8(mL);
+    }
+    T.psi_hi.ensure(size_t(std::max(np, 8LL)) * 2);
+    T.psi_lo.ensure(size_t(std::max(np, 8LL)) * 2);
+    T.psec_dev.ensure(T.psec.size() * sizeof(TcHeff::PsiSec));
+    GBD_CHECK_CUDA(cudaMemcpyAsync(T.psec_dev.p, T.psec.data(), T.psec.size() * sizeof(TcHeff::PsiSec),
+                                   cudaMemcpyHostToDevice, st));
+    // ---- pairs (class, block) with their phase-1 outputs X
+    struct Pair { int c, bl, br, so, si; long long x; };
+    std::vector<Pair> pairs;
+    long long nx = 0;
+    for (size_t c = 0; c < H.OL.cls.size(); ++c) {
+        const OpClass& cl = H.OL.cls[c];
+        const OpClass& cr = H.OR.cls[c];
+        for (size_t bi = 0; bi < cl.blocks.size(); ++bi) {
+            const OpBlock& ob = cl.blocks[bi];
+            int so = H.sector_of(ob.Qo), si = H.sector_of(ob.Qi);
+            if (so < 0 || si < 0) continue;
+            int br = -1;
+            for (size_t x = 0; x < cr.blocks.size(); ++x)
+                if (cr.blocks[x].Qo == ob.Qo && cr.blocks[x].Qi == ob.Qi) br = int(x);
+            if (br < 0) continue;
+            pairs.push_back({int(c), int(bi), br, so, si, nx});
+            nx += (long long)cl.states.size() * H.bL.dim[H.sL[so]] * pad8(H.bR.dim[H.sR[si]]);
+        }
+    }
+    T.x_hi.ensure(size_t(std::max(nx, 8LL)) * 2);
+    T.x_lo.ensure(size_t(std::max(nx, 8LL)) * 2);
+    // ---- tensor maps
+    std::vector<CUtensorMap> maps;
+    auto add_pair_maps = [&](const void* hi, const void* lo, int K, long long rows, int layers, int ld, long long lp,
+                             int box_rows) {
+        int id = int(maps.size());
+        maps.push_back(make_map(hi, K, rows, layers, ld, lp, box_rows));
+        maps.push_back(make_map(lo, K, rows, layers, ld, lp, box_rows));
+        return id;
+    };
+    std::vector<int> psi_map(H.sq.size());
+    for (size_t s = 0; s < H.sq.size(); ++s) {
+        const auto& ps = T.psec[s];
+        psi_map[s] = add_pair_maps(T.psi_hi.as<__nv_bfloat16>() + ps.dst, T.psi_lo.as<__nv_bfloat16>() + ps.dst, ps.mL,
+                                   ps.mR, 0, ps.ldp, 0, BN);
+    }
+    std::vector<KSeg> s1, s2;
+    std::vector<Work> w1, w2;
+    std::vector<Reduce> red;
+    std::vector<std::vector<int>> seg_of_out(H.sq.size());
+    for (const auto& p : pairs) {
+        const OpClass& cl = H.OL.cls[p.c];
+        const int Tn = int(cl.states.size());
+        const int mLo = H.bL.dim[H.sL[p.so]], mLi = H.bL.dim[H.sL[p.si]];
+        const int mRo = H.bR.dim[H.sR[p.so]], mRi = H.bR.dim[H.sR[p.si]];
+        // phase 1: X (Tn*mLo x mRi) = OL_stacked (Tn*mLo x mLi) psi (mLi x mRi), psi^T K-major
+        const long long ol = offL[p.c][p.bl];
+        int mA = add_pair_maps(T.ol_hi.as<__nv_bfloat16>() + ol, T.ol_lo.as<__nv_bfloat16>() + ol, mLi,
+                               (long long)Tn * mLo, 0, pad8(mLi), 0, BM);
+        int sidx = int(s1.size());
+        s1.push_back({mA, psi_map[p.si], 0, 0, mLi, 1, 2, (mLi + BK - 1) / BK});
+        for (long long m0 = 0; m0 < (long long)Tn * mLo; m0 += BM)
+            for (int n0 = 0; n0 < mRi; n0 += BN) {
+                Work w{};
+                w.m0 = int(m0);
+                w.n0 = n0;
+                w.M = Tn * mLo;
+                w.N = mRi;
+                w.seg0 = sidx;
+                w.nseg = 1;
+                w.c0 = 0;
+                w.c1 = s1[sidx].nchunk;
+                w.out_kind = 1;
+                w.promote = 1 << 30;
+                w.ldo = pad8(mRi);
+                w.out_hi = T.x_hi.as<__nv_bfloat16>() + p.x;
+                w.out_lo = T.x_lo.as<__nv_bfloat16>() + p.x;
+                w1.push_back(w);
+            }
+        // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn
+        int mX = add_pair_maps(T.x_hi.as<__nv_bfloat16>() + p.x, T.x_lo.as<__nv_bfloat16>() + p.x, mRi, mLo, Tn,
+                               pad8(mRi), (long long)mLo * pad8(mRi), BM);
+        const long long orr = offR[p.c][p.br];
+        int mO = add_pair_maps(T.or_hi.as<__nv_bfloat16>() + orr, T.or_lo.as<__nv_bfloat16>() + orr, mRi, mRo, Tn,
+                               pad8(mRi), (long long)mRo * pad8(mRi), BN);
+        seg_of_out[p.so].push_back(int(s2.size()));
+        s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
+    }
+    // phase 2 work: per output sector tile, K split into near-equal chunk ranges
+    long long total_chunks = 0;
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        long long c = 0;
+        for (int si : seg_of_out[q]) c += s2[si].nchunk;
+        int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + BN - 1) / BN);
+        total_chunks += c * tiles;
+    }
+    const long long target = std::max<long long>(16, total_chunks / (4 * 152) + 1);
+    std::vector<KSeg> s2o;  // segments re-laid per output sector (contiguous)
+    long long npart = 0;
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        int seg0 = int(s2o.size());
+        int nchunk = 0;
+        for (int si : seg_of_out[q]) { s2o.push_back(s2[si]); nchunk += s2[si].nchunk; }
+        int nseg = int(s2o.size()) - seg0;
+        const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
+        for (int m0 = 0; m0 < mL; m0 += BM)
+            for (int n0 = 0; n0 < mR; n0 += BN) {
+                Reduce r{};
+                r.out = H.yout.as<double>() + H.soff[q];
+                r.ldo = mR;
+                r.m0 = m0;
+                r.n0 = n0;
+                r.M = mL;
+                r.N = mR;
+                r.p0 = int(npart);
+                for (int c0 = 0; c0 < nchunk; c0 += int(target)) {
+                    Work w{};
+                    w.m0 = m0;
+                    w.n0 = n0;
+                    w.M = mL;
+                    w.N = mR;
+                    w.seg0 = seg0;
+                    w.nseg = nseg;
+                    w.c0 = c0;
+                    w.c1 = int(std::min<long long>(nchunk, c0 + target));
+                    w.out_kind = 0;
+                    w.promote = 8;
+                    w.ldo = BN;
+                    w.out_hi = reinterpret_cast<void*>(npart);  // patched to a pointer below
+                    w2.push_back(w);
+                    ++npart;
+                }
+                r.p1 = int(npart);
+                red.push_back(r);
+            }
+    }
+    T.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * BN * sizeof(double));
+    for (auto& w : w2) w.out_hi = T.partial.as<double>() + reinterpret_cast<long long>(w.out_hi) * BM * BN;
+    // ---- upload
+    T.maps.ensure(std::max<size_t>(maps.size(), 1) * sizeof(CUtensorMap));
+    GBD_CHECK_CUDA(cudaMemcpyAsync(T.maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    auto up = [&](DevBuf& d, const void* src, size_t bytes) {
+        d.ensure(std::max<size_t>(bytes, 16));
+        if (bytes) GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, st));
+    };
+    up(T.w1, w1.data(), w1.size() * sizeof(Work));
+    up(T.s1, s1.data(), s1.size() * sizeof(KSeg));
+    up(T.w2, w2.data(), w2.size() * sizeof(Work));
+    up(T.s2, s2o.data(), s2o.size() * sizeof(KSeg));
+    up(T.red, red.data(), red.size() * sizeof(Reduce));
+    T.err.ensure(sizeof(int));
+    GBD_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
+    T.n_w1 = int(w1.size());
+    T.n_w2 = int(w2.size());
+    T.n_red = int(red.size());
+    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    GBD_CHECK_CUDA(cudaStreamSynchronize(st));
+    T.built = true;
+    H.tc_ready = true;
+}
+
+// One mixed-precision product: H.xin (FP64) -> H.yout (FP64).
 void tc_apply(Ctx& C) {
-    (void)C;
-    throw Error(GBD_ERR_ARG, "mixed-precision products are not available in this build");
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    cudaStream_t st = C.cs;
+    if (!T.psec.empty()) {
+        split_psi_kernel<<<dim3(16, unsigned(T.psec.size())), 256, 0, st>>>(
+            H.xin.as<double>(), T.psec_dev.as<TcHeff::PsiSec>(), T.psi_hi.as<__nv_bfloat16>(), T.psi_lo.as<__nv_bfloat16>());
+        count_launch();
+    }
+    if (T.n_w1 > 0) {
+        tc_gemm_kernel<<<T.n_w1, THREADS, SMEM_BYTES, st>>>(T.w1.as<Work>(), T.s1.as<KSeg>(), T.maps.as<CUtensorMap>(),
+                                                           T.err.as<int>());
+        count_launch();
+    }
+    if (T.n_red > 0) {
+        if (T.n_w2 > 0) {
+            tc_gemm_kernel<<<T.n_w2, THREADS, SMEM_BYTES, st>>>(T.w2.as<Work>(), T.s2.as<KSeg>(), T.maps.as<CUtensorMap>(),
+                                                               T.err.as<int>());
+            count_launch();
+        }
+        reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<double>());
+        count_launch();
+    }
+    GBD_CHECK_CUDA(cudaGetLastError());
+}
+
+int tc_error(Ctx& C) {
+    int e = 0;
+    if (C.H.tc.err.p) GBD_CHECK_CUDA(cudaMemcpy(&e, C.H.tc.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    return e;
 }
 
 }  // namespace gbd
