@@ -68,7 +68,9 @@ typedef struct {
     int tsz;            /* twice S_z                                            */
     int D;              /* maximum kept states per bond (truncation)            */
     int precision;      /* GBD_FP64 or GBD_MIXED_BF16X3 (H_eff products only)   */
-    double dav_tol;     /* Davidson residual norm tolerance (FP64 norm)         */
+    double dav_tol;     /* Davidson residual norm tolerance (FP64 norm); mixed
+                           precision stops at max(dav_tol, 2e-5), the rounding
+                           floor of its products                             */
     int dav_max_sub;    /* Davidson subspace size before restart                */
     int dav_keep;       /* Ritz vectors kept at restart                         */
     int dav_max_matvec; /* product limit -> GBD_WARN_NOT_CONVERGED              */
@@ -79,6 +81,10 @@ typedef struct {
                            complementary sums; 0 = automatic (L/2 + 1)         */
     int io_timeout_ms;  /* bound on any host wait for an IO event              */
     unsigned long long seed; /* random initial MPS when none is imported       */
+    int mixed_fp64_blocks; /* mixed products: the two block Hamiltonian terms
+                              (H_left x 1, 1 x H_right) run in FP64           */
+    int mixed_polish;   /* mixed Davidson: the reported energy is the Rayleigh
+                           quotient of the final vector under one FP64 product */
 } gbd_config;
 
 typedef struct {

@@ -33,7 +33,8 @@ class Config(C.Structure):
     _fields_ = [("L", C.c_int), ("N", C.c_int), ("tsz", C.c_int), ("D", C.c_int), ("precision", C.c_int),
                 ("dav_tol", C.c_double), ("dav_max_sub", C.c_int), ("dav_keep", C.c_int),
                 ("dav_max_matvec", C.c_int), ("offload", C.c_int), ("device", C.c_int),
-                ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong)]
+                ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong),
+                ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int)]
 
 
 class SectorInfo(C.Structure):
@@ -162,13 +163,15 @@ class Context:
     """One library context: integrals, MPS, environments, two-site position."""
 
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
-                 dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345):
+                 dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
+                 mixed_fp64_blocks=True, mixed_polish=True):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
         cfg.offload, cfg.device, cfg.dav_tol = int(offload), device, dav_tol
         cfg.dav_max_sub, cfg.dav_keep, cfg.dav_max_matvec = dav_max_sub, dav_keep, dav_max_matvec
         cfg.switch_cut, cfg.io_timeout_ms, cfg.seed = switch_cut, io_timeout_ms, seed
+        cfg.mixed_fp64_blocks, cfg.mixed_polish = int(mixed_fp64_blocks), int(mixed_polish)
         h = C.c_void_p()
         _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
         self.h = h

@@ -56,6 +56,8 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->switch_cut = 0;
     cfg->io_timeout_ms = 120000;
     cfg->seed = 12345;
+    cfg->mixed_fp64_blocks = 1;
+    cfg->mixed_polish = 1;
     return GBD_OK;
 }
 

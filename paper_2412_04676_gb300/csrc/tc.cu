@@ -451,6 +451,80 @@ void tc_prepare(Ctx& C) {
         GBD_CHECK_CUDA(cudaGetLastError());
         GBD_CHECK_CUDA(cudaStreamSynchronize(st));
     }
+    // ---- optional FP64 path for the two block-Hamiltonian terms: their
+    // layers are zeroed in the BF16 copies and applied in FP64 afterwards
+    const int cut = H.b + 1;
+    const int sI = C.mpo.idxI[cut], sF = C.mpo.idxF[cut];
+    T.blk = C.cfg.mixed_fp64_blocks && sI >= 0 && sF >= 0;
+    if (T.blk) {
+        int c0 = H.OL.state_class[sI];
+        GBD_REQUIRE(c0 == H.OL.state_class[sF], GBD_ERR_STATE, "block terms in different classes");
+        const int Tn = int(H.OL.cls[c0].states.size());
+        const int lay[2] = {H.OL.state_layer[sI], H.OL.state_layer[sF]};
+        std::vector<long long> xoff(H.sq.size() * 2);
+        long long xt = 0;
+        for (size_t q = 0; q < H.sq.size(); ++q)
+            for (int k = 0; k < 2; ++k) {
+                xoff[q * 2 + k] = xt;
+                xt += (long long)H.bL.dim[H.sL[q]] * H.bR.dim[H.sR[q]];
+            }
+        T.blk_x.ensure(size_t(std::max(xt, 1LL)) * 8);
+        T.blk_a.clear();
+        T.blk_b.clear();
+        for (int side = 0; side < 2; ++side) {
+            const OpSet& O = side == 0 ? H.OL : H.OR;
+            DevBuf& hi = side == 0 ? T.ol_hi : T.or_hi;
+            DevBuf& lo = side == 0 ? T.ol_lo : T.or_lo;
+            const auto& off = side == 0 ? offL : offR;
+            for (size_t i = 0; i < O.cls[c0].blocks.size(); ++i) {
+                const OpBlock& bb = O.cls[c0].blocks[i];
+                const long long per = (long long)bb.rows * pad8(bb.cols);
+                for (int k = 0; k < 2; ++k) {
+                    GBD_CHECK_CUDA(cudaMemsetAsync(hi.as<__nv_bfloat16>() + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+                    GBD_CHECK_CUDA(cudaMemsetAsync(lo.as<__nv_bfloat16>() + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+                }
+            }
+        }
+        for (size_t q = 0; q < H.sq.size(); ++q) {
+            int bl = -1, br = -1;
+            for (size_t x = 0; x < H.OL.cls[c0].blocks.size(); ++x)
+                if (H.OL.cls[c0].blocks[x].Qo == H.sq[q] && H.OL.cls[c0].blocks[x].Qi == H.sq[q]) bl = int(x);
+            for (size_t x = 0; x < H.OR.cls[c0].blocks.size(); ++x)
+                if (H.OR.cls[c0].blocks[x].Qo == H.sq[q] && H.OR.cls[c0].blocks[x].Qi == H.sq[q]) br = int(x);
+            if (bl < 0 || br < 0) continue;
+            const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
+            std::vector<GemmSeg> segB;
+            for (int k = 0; k < 2; ++k) {
+                GemmTask ta{};
+                ta.C = T.blk_x.as<double>() + xoff[q * 2 + k];
+                ta.ldc = mR; ta.M = mL; ta.N = mR; ta.nbatch = 1;
+                GemmSeg ga{};
+                ga.A = H.OL.data.as<double>() + H.OL.cls[c0].blocks[bl].off + (long long)lay[k] * mL * mL;
+                ga.lda = mL;
+                ga.B = H.xin.as<double>() + H.soff[q];
+                ga.ldb = mR; ga.K = mL; ga.T = 1; ga.coef = 1.0;
+                T.blk_a.add_task(ta, {ga});
+                GemmSeg gb{};
+                gb.A = T.blk_x.as<double>() + xoff[q * 2 + k];
+                gb.lda = mR;
+                gb.B = H.OR.data.as<double>() + H.OR.cls[c0].blocks[br].off + (long long)lay[k] * mR * mR;
+                gb.ldb = mR; gb.transB = 1; gb.K = mR; gb.T = 1; gb.coef = 1.0;
+                segB.push_back(gb);
+            }
+            GemmTask tb{};
+            tb.C = H.yout.as<double>() + H.soff[q];
+            tb.ldc = mR; tb.M = mL; tb.N = mR; tb.nbatch = 1; tb.beta = 1.0;
+            T.blk_b.add_task(tb, segB);
+        }
+        std::vector<std::pair<const void*, size_t>> bufs = {{H.OL.data.p, size_t(H.OL.total) * 8},
+                                                            {H.OR.data.p, size_t(H.OR.total) * 8},
+                                                            {T.blk_x.p, T.blk_x.bytes}, {H.xin.p, H.xin.bytes},
+                                                            {H.yout.p, H.yout.bytes}};
+        T.blk_a.check(bufs, "mixed/block-a");
+        T.blk_b.check(bufs, "mixed/block-b");
+        T.blk_a.upload(st);
+        T.blk_b.upload(st);
+    }
     // ---- psi^T sectors
     long long np = 0;
     for (size_t s = 0; s < H.sq.size(); ++s) {
@@ -637,6 +711,10 @@ void tc_apply(Ctx& C) {
         }
         reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<double>());
         count_launch();
+    }
+    if (T.blk) {
+        T.blk_a.launch(st);
+        T.blk_b.launch(st);
     }
     GBD_CHECK_CUDA(cudaGetLastError());
 }

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "core.h"
+#include "kernels.h"
 
 namespace gbd {
 
@@ -68,6 +69,9 @@ struct TcHeff {
     std::vector<PsiSec> psec;
     DevBuf psec_dev;
     double bytes_ops = 0.0;                 // BF16 operator bytes (hi + lo)
+    GemmPlan blk_a, blk_b;                  // FP64 block-Hamiltonian terms (optional)
+    DevBuf blk_x;
+    bool blk = false;
 };
 
 void tc_prepare(Ctx& C);
