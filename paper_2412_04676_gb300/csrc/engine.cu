@@ -162,12 +162,30 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         }
         links[id].W[size_t(li) * out.cls[co].states.size() + lo] += e.v;
     }
+    // a link whose every output layer has at most one input layer is a set
+    // of scaled copies; the others (complementary sums) are dense GEMMs
+    std::vector<char> sparse(links.size(), 1);
+    std::vector<std::vector<std::pair<int, double>>> col_src(links.size());
+    for (size_t i = 0; i < links.size(); ++i) {
+        const int Tin = int(Ein.cls[links[i].ci].states.size());
+        const int Tout = int(out.cls[links[i].co].states.size());
+        auto& cs = col_src[i];
+        cs.assign(Tout, {-1, 0.0});
+        for (int a = 0; a < Tin && sparse[i]; ++a)
+            for (int c = 0; c < Tout; ++c) {
+                double v = links[i].W[size_t(a) * Tout + c];
+                if (v == 0.0) continue;
+                if (cs[c].first >= 0) { sparse[i] = 0; break; }
+                cs[c] = {a, v};
+            }
+        if (!sparse[i]) cs.clear();
+    }
     std::map<std::tuple<int, int, int>, std::vector<int>> by_cst;  // (co, s, t) -> links
     long long wtot = 0;
     for (size_t i = 0; i < links.size(); ++i) {
         by_cst[std::make_tuple(links[i].co, links[i].s, links[i].t)].push_back(int(i));
         links[i].doff = wtot;
-        wtot += (long long)links[i].W.size();
+        if (!sparse[i]) wtot += (long long)links[i].W.size();
     }
     // output blocks and their sub-block tasks
     struct Sub {
@@ -202,9 +220,10 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         }
     }
     alloc_env(C, out);
-    // upload coefficient matrices
+    // upload coefficient matrices of the dense links
     std::vector<double> wall(size_t(std::max<long long>(wtot, 1)));
-    for (const auto& L : links) std::copy(L.W.begin(), L.W.end(), wall.begin() + L.doff);
+    for (size_t i = 0; i < links.size(); ++i)
+        if (!sparse[i]) std::copy(links[i].W.begin(), links[i].W.end(), wall.begin() + links[i].doff);
     C.scratch_w.ensure(wall.size() * sizeof(double));
     GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_w.p, wall.data(), wall.size() * sizeof(double), cudaMemcpyHostToDevice, C.cs));
     const double* dW = C.scratch_w.as<double>();
@@ -212,12 +231,15 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     double* dout = out.data.as<double>();
     GemmPlan& P = C.plan_a;
     P.clear();
+    std::vector<CopyItem> items;
+    std::vector<CopySrc> srcs;
     for (const auto& sub : subs) {
         const OpClass& oc = out.cls[sub.cls];
         const OpBlock& ob = oc.blocks[sub.blk];
         int Tout = int(oc.states.size());
+        double* dsub = dout + ob.off + (long long)sub.off_r * ob.cols + sub.off_c;
         GemmTask t{};
-        t.C = dout + ob.off + (long long)sub.off_r * ob.cols + sub.off_c;
+        t.C = dsub;
         t.ldc = (long long)ob.rows * ob.cols;
         t.ldr = ob.cols;
         t.M = Tout;
@@ -226,10 +248,18 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         t.nbatch = 1;
         t.beta = 0.0;
         std::vector<GemmSeg> segs;
+        std::vector<std::vector<CopySrc>> per_layer(Tout);
         for (auto& pr : sub.src) {
             const Link& L = links[pr.first];
             const OpClass& ic = Ein.cls[L.ci];
             const OpBlock& ib = ic.blocks[pr.second];
+            if (sparse[pr.first]) {
+                const auto& cs = col_src[pr.first];
+                for (int c = 0; c < Tout; ++c)
+                    if (cs[c].first >= 0)
+                        per_layer[c].push_back({din + ib.off + (long long)cs[c].first * ib.rows * ib.cols, cs[c].second});
+                continue;
+            }
             GemmSeg g{};
             g.A = dW + L.doff;
             g.lda = Tout;
@@ -242,12 +272,40 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             g.coef = 1.0;
             segs.push_back(g);
         }
-        P.add_task(t, segs);
+        if (!segs.empty()) P.add_task(t, segs);
+        for (int c = 0; c < Tout; ++c) {
+            if (per_layer[c].empty()) continue;
+            CopyItem it{};
+            it.dst = dsub + (long long)c * ob.rows * ob.cols;
+            it.ldr = ob.cols;
+            it.rows = sub.rows;
+            it.cols = sub.cols;
+            it.src0 = int(srcs.size());
+            it.nsrc = int(per_layer[c].size());
+            for (auto& x : per_layer[c]) srcs.push_back(x);
+            items.push_back(it);
+        }
     }
     P.check({{C.scratch_w.p, C.scratch_w.bytes}, {Ein.data.p, size_t(Ein.total) * 8}, {out.data.p, size_t(out.total) * 8}},
             "enlarge");
+    // host-side bounds check of the copies
+    for (const auto& it : items) {
+        const char* lo = reinterpret_cast<const char*>(out.data.p);
+        const char* a = reinterpret_cast<const char*>(it.dst);
+        const char* e = reinterpret_cast<const char*>(it.dst + (long long)(it.rows - 1) * it.ldr + it.cols);
+        GBD_REQUIRE(a >= lo && e <= lo + size_t(out.total) * 8, GBD_ERR_STATE, "enlarge: copy outside its block");
+    }
     P.upload(C.cs);
     P.launch(C.cs);
+    if (!items.empty()) {
+        C.scratch_items.ensure(items.size() * sizeof(CopyItem));
+        C.scratch_srcs.ensure(std::max<size_t>(srcs.size(), 1) * sizeof(CopySrc));
+        GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_items.p, items.data(), items.size() * sizeof(CopyItem),
+                                       cudaMemcpyHostToDevice, C.cs));
+        GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_srcs.p, srcs.data(), srcs.size() * sizeof(CopySrc), cudaMemcpyHostToDevice,
+                                       C.cs));
+        copy_sum(C.scratch_items.as<CopyItem>(), int(items.size()), C.scratch_srcs.as<CopySrc>(), C.cs);
+    }
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
 }
 

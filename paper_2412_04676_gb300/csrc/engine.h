@@ -90,7 +90,7 @@ struct Ctx {
     int psi_b = -1;
     // scratch
     GemmPlan plan_a, plan_b, plan_c;
-    DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small;
+    DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small, scratch_items, scratch_srcs;
     DevBuf dav_V, dav_AV, dav_r, dav_t, dav_x, dav_ax, dav_tmp;
     DevBuf stage;  // device staging for pack/unpack through pageable memory
     // statistics

@@ -327,6 +327,29 @@ void fill_zero(double* p, long long n, cudaStream_t st) {
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
+// ============================================================== scaled copies
+namespace {
+__global__ void copy_sum_kernel(const CopyItem* __restrict__ items, const CopySrc* __restrict__ srcs) {
+    const CopyItem it = items[blockIdx.x];
+    const int n = it.rows * it.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        double v = 0.0;
+        for (int k = it.src0; k < it.src0 + it.nsrc; ++k) v = fma(srcs[k].coef, srcs[k].src[e], v);
+        const int r = e / it.cols, c = e % it.cols;
+        it.dst[(long long)r * it.ldr + c] += v;
+    }
+}
+}  // namespace
+
+void copy_sum(const CopyItem* d_items, int n_items, const CopySrc* d_srcs, cudaStream_t st) {
+    for (int i0 = 0; i0 < n_items; i0 += 0x7FFFFFF) {
+        int n = std::min(n_items - i0, 0x7FFFFFF);
+        copy_sum_kernel<<<n, 128, 0, st>>>(d_items + i0, d_srcs);
+        count_launch();
+    }
+    GBD_CHECK_CUDA(cudaGetLastError());
+}
+
 // ============================================================== H_eff diagonal
 namespace {
 __global__ void diag_kernel(const DiagTask* __restrict__ tasks, const DiagSeg* __restrict__ segs) {

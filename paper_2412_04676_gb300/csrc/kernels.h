@@ -107,6 +107,19 @@ void pack_launch(unsigned char* stream_base, const unsigned char* d_headers, con
 void unpack_launch(const unsigned char* stream_base, const PackItem* d_items, const PackChunk* d_chunks,
                    int n_chunks, unsigned long long* d_cks, cudaStream_t st);
 
+// ------------------------------------------------------------------ scaled copies
+// dst (rows x cols, row stride ldr) += sum_k coef_k * src_k (contiguous rows x cols)
+struct CopySrc {
+    const double* src;
+    double coef;
+};
+struct CopyItem {
+    double* dst;
+    long long ldr;
+    int rows, cols, src0, nsrc;
+};
+void copy_sum(const CopyItem* d_items, int n_items, const CopySrc* d_srcs, cudaStream_t st);
+
 // ------------------------------------------------------------------ misc
 // Count of this library's kernel launches (incremented by every launcher).
 unsigned long long launch_count();

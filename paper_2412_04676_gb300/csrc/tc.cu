@@ -6,8 +6,9 @@
 // once into BF16 hi + lo (x = hi + lo + O(2^-18 x)) and each tile computes
 // A_hi B_hi + A_hi B_lo + A_lo B_hi with tcgen05.mma (kind::f16, FP32
 // accumulation in TMEM).  The accumulator is promoted to FP64 registers
-// every `promote` K chunks through two ping-pong TMEM buffers, so the long
-// phase-2 reductions do not accumulate FP32 rounding.  Operands reach shared
+// every `promote` K chunks through two ping-pong TMEM buffers into FP32
+// (hi, lo) two-sum pairs, so the long phase-2 reductions do not accumulate
+// FP32 rounding.  Operands reach shared
 // memory through TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
 // three-stage mbarrier pipeline; one thread issues TMA, one issues MMA, eight
 // warps drain TMEM.  Zero fill of TMA boxes handles ragged sector edges.
@@ -107,6 +108,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -244,25 +254,35 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             }
         }
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> FP64 registers
+        // ---------------- epilogue: TMEM -> FP32 (hi, lo) pairs
+        // GB300's FP64 pipe is narrow, so the promotion of each TMEM partial
+        // sum is an error-free FP32 two-sum into a (hi, lo) pair (about 48
+        // significant bits); FP64 appears only in the split-K reduction.
         const int quad = warp & 3;          // TMEM lane quadrant this warp may access
         const int half = (warp - 2) >> 2;   // column half
         const int row = quad * 32 + lane;
-        double acc[BN / 2];
+        float ah[BN / 2], al[BN / 2];
 #pragma unroll
-        for (int i = 0; i < BN / 2; ++i) acc[i] = 0.0;
+        for (int i = 0; i < BN / 2; ++i) { ah[i] = 0.f; al[i] = 0.f; }
         for (int dd = 0; dd < ndrain; ++dd) {
             const int buf = dd & 1;
             bool ok = mbar_wait(smem_u32(&tfull[buf]), (dd >> 1) & 1);
             if (!ok) { atomicExch(err, 4); abort_s = 1; break; }
             tc_fence_after();
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + half * (BN / 2) + c * 32);
-                tmem_ld32(taddr, r);
+            for (int c = 0; c < 4; ++c) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + half * (BN / 2) + c * 16);
+                tmem_ld16(taddr, r);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) acc[c * 32 + i] += double(__uint_as_float(r[i]));
+                for (int i = 0; i < 16; ++i) {
+                    const float x = __uint_as_float(r[i]);
+                    const float a = ah[c * 16 + i];
+                    const float sum = a + x;
+                    const float bb = sum - a;
+                    al[c * 16 + i] += (a - (sum - bb)) + (x - bb);
+                    ah[c * 16 + i] = sum;
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -271,29 +291,55 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         const int gr = w.m0 + row;
         const int gc0 = w.n0 + half * (BN / 2);
         if (w.out_kind == 0) {
-            double* out = reinterpret_cast<double*>(w.out_hi) + (long long)row * BN + half * (BN / 2);
+            // partial tile of (hi, lo) pairs, column-pair-major: a warp writes
+            // 512 contiguous bytes per store
+            float4* out = reinterpret_cast<float4*>(w.out_hi);
 #pragma unroll
-            for (int i = 0; i < BN / 2; i += 2) *reinterpret_cast<double2*>(out + i) = make_double2(acc[i], acc[i + 1]);
+            for (int i = 0; i < BN / 2; i += 2)
+                out[(long long)(half * (BN / 4) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
         } else if (w.out_kind == 1) {
-            if (gr < w.M) {
-                __nv_bfloat16* oh = reinterpret_cast<__nv_bfloat16*>(w.out_hi) + (long long)gr * w.ldo;
-                __nv_bfloat16* ol = reinterpret_cast<__nv_bfloat16*>(w.out_lo) + (long long)gr * w.ldo;
+            // BF16 hi / lo through shared memory (the pipeline stages are idle
+            // now), then coalesced 16-byte stores of whole rows
+            constexpr int RS = BN * 2 + 16;  // padded row stride in bytes
+            uint8_t* sh = smem;
+            uint8_t* sl = smem + BM * RS;
 #pragma unroll
-                for (int i = 0; i < BN / 2; ++i) {
-                    const int gc = gc0 + i;
-                    if (gc < w.N) {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(float(acc[i]));
-                        oh[gc] = h;
-                        ol[gc] = __float2bfloat16_rn(float(acc[i] - double(__bfloat162float(h))));
-                    }
+            for (int i = 0; i < BN / 2; i += 8) {
+                uint32_t ph[4], pl[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    // x - bf16(x) is exact in FP32, so the split needs no FP64
+                    const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                    ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+                    pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
                 }
+                const int cb = (half * (BN / 2) + i) * 2;
+                *reinterpret_cast<uint4*>(sh + row * RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4*>(sl + row * RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+            const int et = threadIdx.x - 64;                  // 0..255
+            const int vpr = BN / 8;                           // 16-byte vectors per row
+            const long long ldo = w.ldo;
+            for (int v = et; v < BM * vpr; v += 256) {
+                const int r = v / vpr, c8 = (v % vpr) * 8;
+                const int grow = w.m0 + r, gcol = w.n0 + c8;
+                if (grow >= w.M || gcol >= ldo) continue;
+                const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * RS + c8 * 2);
+                const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * RS + c8 * 2);
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_hi) + grow * ldo + gcol) = hv;
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_lo) + grow * ldo + gcol) = lv;
             }
         } else {
             if (gr < w.M) {
                 double* o = reinterpret_cast<double*>(w.out_hi) + (long long)gr * w.ldo;
 #pragma unroll
                 for (int i = 0; i < BN / 2; ++i)
-                    if (gc0 + i < w.N) o[gc0 + i] = acc[i];
+                    if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
             }
         }
     }
@@ -342,14 +388,20 @@ __global__ void split_psi_kernel(const double* __restrict__ psi, const TcHeff::P
     }
 }
 
-__global__ void reduce_kernel(const Reduce* __restrict__ red, const double* __restrict__ partial) {
+// partial tiles hold FP32 (hi, lo) pairs, column-pair-major: element (i, j)
+// at pair index ((j / 2) * BM + i) * 2 + (j % 2)
+__global__ void reduce_kernel(const Reduce* __restrict__ red, const float2* __restrict__ partial) {
     const Reduce r = red[blockIdx.x];
     for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
         const int i = e / BN, j = e % BN;
         const int gi = r.m0 + i, gj = r.n0 + j;
         if (gi >= r.M || gj >= r.N) continue;
+        const long long idx = ((long long)(j / 2) * BM + i) * 2 + (j % 2);
         double v = 0.0;
-        for (int p = r.p0; p < r.p1; ++p) v += partial[(long long)p * BM * BN + e];
+        for (int p = r.p0; p < r.p1; ++p) {
+            const float2 x = partial[(long long)p * BM * BN + idx];
+            v += double(x.x) + double(x.y);
+        }
         r.out[(long long)gi * r.ldo + gj] = v;
     }
 }
@@ -663,8 +715,8 @@ void tc_prepare(Ctx& C) {
                 red.push_back(r);
             }
     }
-    T.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * BN * sizeof(double));
-    for (auto& w : w2) w.out_hi = T.partial.as<double>() + reinterpret_cast<long long>(w.out_hi) * BM * BN;
+    T.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * BN * sizeof(float2));
+    for (auto& w : w2) w.out_hi = T.partial.as<float2>() + reinterpret_cast<long long>(w.out_hi) * BM * BN;
     // ---- upload
     T.maps.ensure(std::max<size_t>(maps.size(), 1) * sizeof(CUtensorMap));
     GBD_CHECK_CUDA(cudaMemcpyAsync(T.maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
@@ -709,7 +761,7 @@ void tc_apply(Ctx& C) {
                                                                T.err.as<int>());
             count_launch();
         }
-        reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<double>());
+        reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<float2>());
         count_launch();
     }
     if (T.blk) {
