@@ -266,6 +266,36 @@ int gbd_env_import(gbd_ctx* ctx, int side, int cut, int ncls, const int* class_m
  * block padded to an even number of doubles).  *elems gets the arena size. */
 int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, size_t* elems);
 
+/* Allocation-free pack.  The paper has no counterpart to this entry point.
+ *
+ * Serialises a block-sparse environment that lives in caller-owned device
+ * memory into caller-owned device memory, in the package format of
+ * gbd_pack_env, without allocating anything: no cudaMalloc, cudaFree or
+ * allocating library routine is called.  It is meant for callers that cannot
+ * allocate device memory: a host runtime whose device memory is entirely
+ * owned by another allocator (e.g. a framework's caching allocator that has
+ * reserved the whole GPU), or a latency-critical offload thread that must
+ * not take the implicit device synchronisation cudaMalloc/cudaFree can cause.
+ *
+ * arena: device pointer to the environment in the canonical layout of
+ * gbd_env_export (blocks class-major, each padded to an even number of
+ * doubles); class_meta / block_meta as for gbd_env_import (host memory);
+ * side and length are written into every header; dst: device memory of at
+ * least the size written to *bytes (too small -> GBD_ERR_ARG with the
+ * required size); stream: a cudaStream_t (NULL = legacy default stream); the
+ * call returns once the stream has finished the pack.
+ *
+ * Scratch: one file-scope device array of 8 MiB, which every GPU that loads
+ * this library holds until the process exits.  Limits: 32768 packages and
+ * 65536 chunks of 64 KB; larger environments -> GBD_ERR_ARG.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents (the
+ * checksum accumulators are cleared at the start of every call); calls that
+ * overlap on the GPU (other streams, other threads) race on it. */
+int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const int* class_meta, int nblk,
+                     const int* block_meta, void* dst, size_t cap, size_t* bytes, void* stream);
+
 /* Offload statistics of the context so far. */
 int gbd_io_stats(gbd_ctx* ctx, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack);
 

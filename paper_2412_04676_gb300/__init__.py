@@ -100,6 +100,8 @@ _SIGS = {
     "gbd_env_export": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
+    "gbd_pack_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, C.c_size_t,
+                                   C.POINTER(C.c_size_t), _P]),
 }
 
 
@@ -157,6 +159,37 @@ def site_arrays(site):
     data = np.concatenate([np.ascontiguousarray(site[k], dtype=np.float64).ravel() for k in keys]) \
         if keys else np.zeros(0)
     return np.ascontiguousarray(meta), np.ascontiguousarray(data)
+
+
+def env_metadata(classes):
+    """(class_meta, block_meta, data) arrays of an environment in canonical order."""
+    cm = np.array([[c["dq"][0], c["dq"][1], len(c["layers"])] for c in classes], dtype=np.int32).reshape(-1, 3)
+    bm, data = [], []
+    for ci, c in enumerate(classes):
+        for (qo, qi, r, cc, d) in c["blocks"]:
+            bm.append([ci, qo[0], qo[1], qi[0], qi[1], r, cc])
+            data.append(np.ascontiguousarray(d, dtype=np.float64).ravel())
+    bm = np.array(bm, dtype=np.int32).reshape(-1, 7)
+    data = np.concatenate(data) if data else np.zeros(0)
+    return np.ascontiguousarray(cm), np.ascontiguousarray(bm), np.ascontiguousarray(data)
+
+
+def pack_noalloc(side, length, arena, class_meta, block_meta, dst, stream=None):
+    """Allocation-free pack of a caller-owned device arena into a caller-owned device buffer.
+
+    Returns the number of bytes written; raises GbdError (with the required size
+    in ``.required``) when dst is too small or a limit is exceeded.
+    """
+    need = C.c_size_t()
+    nbytes = dst.numel() if hasattr(dst, "numel") else dst.nbytes
+    rc = lib().gbd_pack_noalloc(side, length, _ptr(arena), class_meta.shape[0], _ptr(class_meta),
+                                block_meta.shape[0], _ptr(block_meta), _ptr(dst), nbytes, C.byref(need),
+                                C.c_void_p(stream))
+    if rc < 0:
+        err = GbdError(rc, lib().gbd_last_error().decode())
+        err.required = need.value
+        raise err
+    return need.value
 
 
 class Context:
@@ -303,15 +336,7 @@ class Context:
 
     def env_import(self, side, cut, classes):
         """classes as produced by inputs.make_env_blocks (canonical order)."""
-        cm = np.array([[c["dq"][0], c["dq"][1], len(c["layers"])] for c in classes], dtype=np.int32).reshape(-1, 3)
-        bm, data = [], []
-        for ci, c in enumerate(classes):
-            for (qo, qi, r, cc, d) in c["blocks"]:
-                bm.append([ci, qo[0], qo[1], qi[0], qi[1], r, cc])
-                data.append(np.ascontiguousarray(d, dtype=np.float64).ravel())
-        bm = np.array(bm, dtype=np.int32).reshape(-1, 7)
-        data = np.concatenate(data) if data else np.zeros(0)
-        cm, bm, data = (np.ascontiguousarray(x) for x in (cm, bm, data))
+        cm, bm, data = env_metadata(classes)
         _check(lib().gbd_env_import(self.h, side, cut, cm.shape[0], _ptr(cm), bm.shape[0], _ptr(bm), _ptr(data)))
 
     def env_export(self, side, cut):

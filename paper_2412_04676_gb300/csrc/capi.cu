@@ -30,6 +30,11 @@ template <class F> int guard(F&& f) {
     }
 }
 
+}  // namespace
+
+void gbd::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
 Ctx& ctx(gbd_ctx* c) {
     if (!c) throw Error(GBD_ERR_ARG, "null context");
     return c->C;

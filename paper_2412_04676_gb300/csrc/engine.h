@@ -121,4 +121,7 @@ void pack_env(Ctx& C, const OpSet& E, unsigned char* dst, bool dst_device_or_pin
 void unpack_env(Ctx& C, OpSet& E, const unsigned char* src, size_t bytes, bool src_device_or_pinned, cudaStream_t st);
 OpSet* env_of(Ctx& C, int side, int cut, bool create);
 
+// thread-local message returned by gbd_last_error()
+void set_last_error(const char* msg);
+
 }  // namespace gbd
