@@ -96,7 +96,6 @@ def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
     Returns (useful TFLOP/s, cores, description, per-step seconds).
     """
     import numpy as np
-    from threadpoolctl import threadpool_info
 
     import inputs
     from oracle import dmrg as R
@@ -129,11 +128,12 @@ def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
             break
         if max_steps is None and time.perf_counter() - t0 >= seconds:
             break
-    cores = 0
+    cores = os.cpu_count() or 0
     try:
-        cores = max(int(x.get("num_threads", 0)) for x in threadpool_info())
+        from threadpoolctl import threadpool_info
+        cores = max(int(x.get("num_threads", 0)) for x in threadpool_info()) or cores
     except Exception:
-        cores = os.cpu_count() or 0
+        pass
     desc = (f"oracle H_eff psi at L=10,N=10,D=256 (config 1, mid-chain cut), dim {He.dim}, "
             f"{len(times)} products in {sum(times):.1f} s; the oracle cannot build the L=30, D=1024 "
             f"environments in bounded time")
@@ -215,6 +215,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     clocks.start()
     l0 = g.launch_count()
+    tm0 = ctx.timers()
     stats = []
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -222,6 +223,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     l1 = g.launch_count()
+    tm1 = ctx.timers()
     clk = clocks.stop()
     barrier()
     flops = sum(s["useful_flops"] for s in stats)
@@ -308,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
                    "ms_io_exposed": sum(s["ms_io_exposed"] for s in stats),
                    "bytes_packed_per_step": sum(s["bytes_packed"] for s in stats) / args.steps,
                    "ms_truncate": sum(s["ms_truncate"] for s in stats),
-                   "ms_renorm": sum(s["ms_renorm"] for s in stats)},
+                   "ms_renorm": sum(s["ms_renorm"] for s in stats),
+                   "timers_ms": {k: tm1[k] - tm0[k] for k in tm1}},
     }
     print(json.dumps(line), flush=True)
     if cpu_proc is not None:
@@ -322,7 +325,7 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
     ap.add_argument("--no-offload", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

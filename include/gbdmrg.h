@@ -296,6 +296,13 @@ int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, siz
 int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const int* class_meta, int nblk,
                      const int* block_meta, void* dst, size_t cap, size_t* bytes, void* stream);
 
+/* Accumulated phase timers of the context in ms, in this order: enlargement
+ * planning (host), enlargement kernels, renormalisation planning (host),
+ * renormalisation kernels, per-sector eigensolves, FP64 polish products,
+ * mixed-precision operand preparation, Davidson host time (reserved).
+ * *n gets the count; out may be NULL. */
+int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
+
 /* Offload statistics of the context so far. */
 int gbd_io_stats(gbd_ctx* ctx, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack);
 

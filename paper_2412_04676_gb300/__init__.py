@@ -100,6 +100,7 @@ _SIGS = {
     "gbd_env_export": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
+    "gbd_timers": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     "gbd_pack_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, C.c_size_t,
                                    C.POINTER(C.c_size_t), _P]),
 }
@@ -347,6 +348,15 @@ class Context:
         out = np.zeros(max(n.value, 1))
         _check(lib().gbd_env_export(self.h, side, cut, _ptr(out), out.size, C.byref(n)))
         return out[:n.value]
+
+    TIMERS = ["enlarge_host", "enlarge_dev", "renorm_host", "renorm_dev", "eigensolve", "polish", "tc_prepare",
+              "davidson_host"]
+
+    def timers(self):
+        out = np.zeros(16)
+        n = C.c_int()
+        _check(lib().gbd_timers(self.h, _ptr(out), 16, C.byref(n)))
+        return dict(zip(self.TIMERS, out[:n.value]))
 
     def io_stats(self):
         v = [C.c_double() for _ in range(4)]

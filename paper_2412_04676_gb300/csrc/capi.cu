@@ -394,6 +394,18 @@ int gbd_env_export(gbd_ctx* c, int side, int cut, double* out, size_t cap, size_
     });
 }
 
+int gbd_timers(gbd_ctx* c, double* out, int cap, int* n) {
+    return guard([&] {
+        Ctx& C = ctx(c);
+        if (n) *n = Ctx::T_COUNT;
+        if (out) {
+            GBD_REQUIRE(cap >= Ctx::T_COUNT, GBD_ERR_ARG, "output too small");
+            for (int i = 0; i < Ctx::T_COUNT; ++i) out[i] = C.timers[i];
+        }
+        return GBD_OK;
+    });
+}
+
 int gbd_io_stats(gbd_ctx* c, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack) {
     return guard([&] {
         Ctx& C = ctx(c);

@@ -27,6 +27,12 @@
 
 namespace gbd {
 
+namespace {
+double wall_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
 // ============================================================== bases
 EBasis left_enlarged(const Bond& b) {
     std::map<Q, std::vector<Seg>> m;
@@ -127,6 +133,7 @@ struct Link {
 // basis (cut-k bond) + orbital k.  side 1: Ein = right environment at cut
 // k+1, output = states of cut k on orbital k + (cut-(k+1) bond).
 static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasis& basis) {
+    const double t_host0 = wall_ms();
     const Mpo& M = C.mpo;
     const int out_cut = side == 0 ? k + 1 : k;
     const Bond& bin = C.bonds[side == 0 ? k : k + 1];
@@ -295,6 +302,8 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         const char* e = reinterpret_cast<const char*>(it.dst + (long long)(it.rows - 1) * it.ldr + it.cols);
         GBD_REQUIRE(a >= lo && e <= lo + size_t(out.total) * 8, GBD_ERR_STATE, "enlarge: copy outside its block");
     }
+    const double t_dev0 = wall_ms();
+    C.timers[Ctx::T_ENL_HOST] += t_dev0 - t_host0;
     P.upload(C.cs);
     P.launch(C.cs);
     if (!items.empty()) {
@@ -307,12 +316,14 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         copy_sum(C.scratch_items.as<CopyItem>(), int(items.size()), C.scratch_srcs.as<CopySrc>(), C.cs);
     }
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+    C.timers[Ctx::T_ENL_DEV] += wall_ms() - t_dev0;
 }
 
 // ============================================================== renormalisation
 // Post-processing (Sec. II.B step 3): E_new[t] = U_Q^T O[t] U_Q2 for every
 // block of the enlarged operator set whose two sectors are kept.
 static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
+    const double t_host0 = wall_ms();
     out = OpSet();
     out.side = O.side;
     out.cut = O.cut;
@@ -405,11 +416,14 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
                                                         {out.data.p, size_t(out.total) * 8}};
     PA.check(bufs, "renormalise/A");
     PB.check(bufs, "renormalise/B");
+    const double t_dev0 = wall_ms();
+    C.timers[Ctx::T_REN_HOST] += t_dev0 - t_host0;
     PA.upload(C.cs);
     PA.launch(C.cs);
     PB.upload(C.cs);
     PB.launch(C.cs);
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+    C.timers[Ctx::T_REN_DEV] += wall_ms() - t_dev0;
 }
 
 // ============================================================== setup
@@ -746,7 +760,12 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
     if (precision == GBD_MIXED_BF16X3) {
-        if (!H.tc_ready) tc_prepare(C);
+        if (!H.tc_ready) {
+            const double tt0 = wall_ms();
+            tc_prepare(C);
+            C.timers[Ctx::T_TCPREP] += wall_ms() - tt0;
+            GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
+        }
         tc_apply(C);
     } else {
         H.p1.launch(C.cs);
@@ -996,7 +1015,9 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     if (prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish) {
         // Rayleigh quotient under one FP64 product: the energy error becomes
         // second order in the mixed-precision product error
+        const double tp0 = wall_ms();
         apply_heff_dev(C, x, ax, GBD_FP64);
+        C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
         dots(x, 1, ax, d);
         theta = d[0];
         axpby(ax, r, n, 1.0, 0.0, s);
@@ -1092,6 +1113,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     P.upload(s);
     P.launch(s);
     // eigen-decomposition per sector (FP64, cuSOLVER)
+    const double t_eig0 = wall_ms();
     int lmax = 0;
     int mmax = *std::max_element(m.begin(), m.end());
     cusolverDnSetStream(C.sol, s);
@@ -1121,6 +1143,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     GBD_CHECK_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, ns * sizeof(int), cudaMemcpyDeviceToHost, s));
     GBD_CHECK_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < ns; ++i) GBD_REQUIRE(hinfo[i] == 0, GBD_ERR_CUDA, "eigensolver did not converge");
+    C.timers[Ctx::T_EIG] += wall_ms() - t_eig0;
     // global selection: descending, at most Dmax, degenerate group at the cut
     // moves the cut down, sqrt(lambda) <= 1e-13 sqrt(lambda_max) dropped
     std::vector<Pick> all;

@@ -99,6 +99,9 @@ struct Ctx {
     double ms_matvec_acc = 0;
     int matvec_count = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // phase timers (ms): host planning and device execution
+    enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_COUNT };
+    double timers[T_COUNT] = {0};
 };
 
 void ensure_cuda(Ctx& C);
