@@ -268,14 +268,31 @@ def run_ours(args, rank, world, local_rank):
     except Exception:
         pass
     flops_mv = info["useful_flops"]
-    achieved = flops_mv / (ms_mv / nmv * 1e-3) / 1e12 if nmv else 0.0
-    if prec == g.FP64:
-        peak, bound, src = args.fp64_peak, "alu", "FP64 FMA pipe, derived (see DESIGN.md)"
-    else:
-        peak = peaks.get("bf16_tflops", 1900.0) / 3.0
-        bound, src = "tensor", "measured bf16 burst / 3 (BF16x3)"
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "H_eff product (phase 1 + phase 2 launches)", "peak_source": src}
+    dt = {k: tm1[k] - tm0[k] for k in tm1}
+    hbm = peaks.get("hbm_gbs", 6787.2)
+    bf16x3 = peaks.get("bf16_tflops", 1908.5) / 3.0
+    n_pol = args.steps if (prec == g.MIXED_BF16X3) else 0
+    ms_pol = dt["polish"] if prec == g.MIXED_BF16X3 else ms_mv
+    n_f64 = n_pol if prec == g.MIXED_BF16X3 else nmv
+    ms_mix = ms_mv - dt["polish"] if prec == g.MIXED_BF16X3 else 0.0
+    n_mix = nmv - n_pol if prec == g.MIXED_BF16X3 else 0
+    fp64_ms = (ms_pol if n_f64 else 0.0) + dt["enlarge_dev"] + dt["renorm_dev"]
+    ach64 = flops_mv * n_f64 / (ms_pol * 1e-3) / 1e12 if n_f64 and ms_pol > 0 else 0.0
+    roof64 = {"bound": "alu", "achieved": ach64, "peak": args.fp64_peak, "unit": "TFLOP/s",
+              "frac": ach64 / args.fp64_peak, "traffic": None,
+              "kernel": "gemm_f64_kernel: FP64 H_eff product (phase-1 + phase-2 launches)",
+              "peak_source": "of measured: cuBLAS DGEMM 8192^3 on this pool"}
+    roof_tc = None
+    if n_mix:
+        ach = flops_mv * n_mix / (ms_mix * 1e-3) / 1e12
+        gbs = info["mixed_bytes"] * n_mix / (ms_mix * 1e-3) / 1e9
+        roof_tc = {"bound": "tensor", "achieved": ach, "peak": bf16x3, "unit": "TFLOP/s", "frac": ach / bf16x3,
+                   "traffic": None, "kernel": "tc_gemm_kernel: BF16x3 H_eff product (split + phase 1 + phase 2 + reduce)",
+                   "peak_source": "of measured: bf16 burst / 3",
+                   "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                "bytes_per_product": info["mixed_bytes"]}}
+    # the dominant kernel by device time in the timed steps
+    roof = roof64 if (fp64_ms >= ms_mix or roof_tc is None) else roof_tc
     cpu = None
     if cpu_q is not None:
         try:
@@ -303,6 +320,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(l1 - l0),
         "roofline": roof,
+        "roofline_tensor": roof_tc,
         "cpu_baseline": cpu,
         "clocks": clk,
         "detail": {"matvec_tflops": achieved, "matvecs": nmv, "ms_matvec": ms_mv, "ms_device": ms_dev,
@@ -311,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
                    "bytes_packed_per_step": sum(s["bytes_packed"] for s in stats) / args.steps,
                    "ms_truncate": sum(s["ms_truncate"] for s in stats),
                    "ms_renorm": sum(s["ms_renorm"] for s in stats),
-                   "timers_ms": {k: tm1[k] - tm0[k] for k in tm1}},
+                   "timers_ms": dt, "ms_fp64_kernels": fp64_ms, "ms_mixed_products": ms_mix}, 
     }
     print(json.dumps(line), flush=True)
     if cpu_proc is not None:
@@ -332,7 +350,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-matvec", type=int, default=40)
-    ap.add_argument("--fp64-peak", type=float, default=1.25)
+    ap.add_argument("--fp64-peak", type=float, default=1.0975)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

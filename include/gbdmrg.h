@@ -101,6 +101,10 @@ typedef struct {
     long long n_gemm;       /* sector GEMMs in one product (both phases)         */
     double useful_flops;    /* 2*m*k*n summed over those GEMMs, counted once     */
     double operator_bytes;  /* FP64 bytes of the two enlarged operator sets      */
+    double mixed_bytes;     /* algorithmic HBM bytes of one mixed product:
+                               BF16 hi+lo operands (4 B/element), the phase-1
+                               intermediate written and read once (4 B each),
+                               psi read and H psi written (FP64)                */
 } gbd_heff_info;
 
 typedef struct {

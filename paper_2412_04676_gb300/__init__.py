@@ -43,7 +43,8 @@ class SectorInfo(C.Structure):
 
 class HeffInfo(C.Structure):
     _fields_ = [("dim", C.c_longlong), ("n_sectors", C.c_int), ("n_terms", C.c_int), ("n_classes", C.c_int),
-                ("n_gemm", C.c_longlong), ("useful_flops", C.c_double), ("operator_bytes", C.c_double)]
+                ("n_gemm", C.c_longlong), ("useful_flops", C.c_double), ("operator_bytes", C.c_double),
+                ("mixed_bytes", C.c_double)]
 
 
 class StepStats(C.Structure):

@@ -169,6 +169,7 @@ int gbd_build_tables(gbd_ctx* c, int b, gbd_sector_info* out, int cap, int* n, g
             info->n_gemm = H.ngemm;
             info->useful_flops = H.flops;
             info->operator_bytes = H.op_bytes;
+            info->mixed_bytes = H.mixed_bytes;
         }
         return GBD_OK;
     });

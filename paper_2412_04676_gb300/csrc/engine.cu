@@ -741,6 +741,16 @@ void setup_heff(Ctx& C, int b) {
         H.p2.add_task(t2, by_out[s]);
     }
     H.flops = H.p1.flops + H.p2.flops;
+    {
+        double elems = 0.0;
+        for (const OpSet* O : {&H.OL, &H.OR})
+            for (const auto& c : O->cls)
+                for (const auto& bb : c.blocks) elems += double(c.states.size()) * bb.rows * bb.cols;
+        double nx = 0.0;
+        for (const auto& p : pairs)
+            nx += double(H.OL.cls[p.c].states.size()) * H.bL.dim[H.sL[p.s_out]] * H.bR.dim[H.sR[p.s_in]];
+        H.mixed_bytes = 4.0 * elems + 8.0 * nx + 16.0 * double(H.dim);
+    }
     std::vector<std::pair<const void*, size_t>> bufs = {{H.OL.data.p, size_t(H.OL.total) * 8},
                                                         {H.OR.data.p, size_t(H.OR.total) * 8},
                                                         {H.X.p, H.X.bytes}, {H.xin.p, H.xin.bytes},

@@ -58,7 +58,7 @@ struct Heff {
     DevBuf X, xin, yout, diag;
     bool diag_ready = false;
     long long ngemm = 0;
-    double flops = 0.0, op_bytes = 0.0;
+    double flops = 0.0, op_bytes = 0.0, mixed_bytes = 0.0;
     TcHeff tc;               // mixed-precision (BF16x3, tcgen05) operands and plans
     bool tc_ready = false;
     int sector_of(const Q& q) const {
