@@ -26,7 +26,11 @@ void count_launch(unsigned n) { g_launches += n; }
 
 // ============================================================== grouped GEMM
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+// 32 x 32 CTA tiles of eight warps; each warp owns a 16 x 8 sub-tile (two
+// rows x two columns per lane) and skips the FMA loop when its sub-tile lies
+// outside the task, and the K loop stops at the task's true K.  GB300's FP64
+// pipe retires about 2 FMA/clk/SM, so padded FMAs cost as much as useful ones.
+constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
 
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTask* __restrict__ tasks,
                                                       const GemmSeg* __restrict__ segs,
@@ -35,12 +39,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTask* __restrict
     __shared__ double Bs[BK][BN + 1];
     const GemmTile tl = tiles[blockIdx.x];
     const GemmTask tk = tasks[tl.task];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wr = (warp >> 2) * 16, wc = (warp & 3) * 8;   // warp sub-tile origin
+    const int lr = lane >> 2, lc = lane & 3;                // lane: rows lr, lr+8; cols lc, lc+4
+    const bool active = (tl.m0 + wr < tk.M) && (tl.n0 + wc < tk.N);
+    double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
 
     for (int s = tk.seg0; s < tk.seg0 + tk.nseg; ++s) {
         const GemmSeg sg = segs[s];
@@ -75,37 +78,34 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTask* __restrict
                     Bs[k][n] = v;
                 }
                 __syncthreads();
-#pragma unroll
-                for (int kk = 0; kk < BK; ++kk) {
-                    double a[4], b[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                if (active) {
+                    const int kend = min(BK, sg.K - k0);
+                    for (int kk = 0; kk < kend; ++kk) {
+                        const double a0 = As[kk][wr + lr], a1 = As[kk][wr + lr + 8];
+                        const double b0 = Bs[kk][wc + lc], b1 = Bs[kk][wc + lc + 4];
+                        acc00 = fma(a0, b0, acc00);
+                        acc01 = fma(a0, b1, acc01);
+                        acc10 = fma(a1, b0, acc10);
+                        acc11 = fma(a1, b1, acc11);
+                    }
                 }
                 __syncthreads();
             }
         }
     }
+    if (!active) return;
     double* C = tk.C + (long long)tl.batch * tk.bC;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int m = tl.m0 + ty + 16 * i;
-        if (m >= tk.M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int n = tl.n0 + tx + 16 * j;
-            if (n >= tk.N) continue;
-            long long off = (long long)m * tk.ldc + (long long)(n / tk.ncols) * tk.ldr + (n % tk.ncols);
-            double v = acc[i][j];
-            if (tk.beta != 0.0) v += tk.beta * C[off];
-            C[off] = v;
-        }
-    }
+    auto store = [&](int m, int n, double v) {
+        if (m >= tk.M || n >= tk.N) return;
+        long long off = (long long)m * tk.ldc + (long long)(n / tk.ncols) * tk.ldr + (n % tk.ncols);
+        if (tk.beta != 0.0) v += tk.beta * C[off];
+        C[off] = v;
+    };
+    const int m0 = tl.m0 + wr + lr, n0 = tl.n0 + wc + lc;
+    store(m0, n0, acc00);
+    store(m0, n0 + 4, acc01);
+    store(m0 + 8, n0, acc10);
+    store(m0 + 8, n0 + 4, acc11);
 }
 
 template <class T>
