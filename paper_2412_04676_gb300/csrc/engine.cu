@@ -436,6 +436,11 @@ void ensure_cuda(Ctx& C) {
     GBD_CHECK_CUDA(cudaEventCreate(&C.ev1));
     if (cusolverDnCreate(&C.sol) != CUSOLVER_STATUS_SUCCESS) throw Error(GBD_ERR_CUDA, "cusolverDnCreate failed");
     cusolverDnSetStream(C.sol, C.cs);
+    for (int i = 0; i < Ctx::kEigStreams; ++i) {
+        GBD_CHECK_CUDA(cudaStreamCreateWithFlags(&C.eig_st[i], cudaStreamNonBlocking));
+        if (cusolverDnCreate(&C.eig_sol[i]) != CUSOLVER_STATUS_SUCCESS) throw Error(GBD_ERR_CUDA, "cusolverDnCreate failed");
+        cusolverDnSetStream(C.eig_sol[i], C.eig_st[i]);
+    }
     C.cuda_ready = true;
 }
 
@@ -448,6 +453,11 @@ void destroy_ctx(Ctx& C) {
     C.hostL.clear();
     C.hostR.clear();
     if (C.sol) cusolverDnDestroy(C.sol);
+    for (int i = 0; i < Ctx::kEigStreams; ++i) {
+        if (C.eig_sol[i]) cusolverDnDestroy(C.eig_sol[i]);
+        if (C.eig_st[i]) cudaStreamDestroy(C.eig_st[i]);
+        C.eig_work[i].release();
+    }
     if (C.ev0) cudaEventDestroy(C.ev0);
     if (C.ev1) cudaEventDestroy(C.ev1);
     C.envL.clear();
@@ -1122,31 +1132,51 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     P.check({{C.psi.p, C.psi.bytes}, {rho.p, rho.bytes}}, "truncate/rho");
     P.upload(s);
     P.launch(s);
-    // eigen-decomposition per sector (FP64, cuSOLVER)
+    // eigen-decomposition per sector (FP64, cuSOLVER), largest sectors first,
+    // spread over several streams so the small solves overlap
     const double t_eig0 = wall_ms();
-    int lmax = 0;
-    int mmax = *std::max_element(m.begin(), m.end());
-    cusolverDnSetStream(C.sol, s);
-    if (cusolverDnDsyevd_bufferSize(C.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mmax, rho.as<double>(),
-                                    mmax, evals.as<double>(), &lmax) != CUSOLVER_STATUS_SUCCESS)
-        throw Error(GBD_ERR_CUDA, "syevd buffer size query failed");
-    DevBuf work;
-    work.ensure(size_t(std::max(lmax, 1)) * sizeof(double));
     std::vector<long long> eoff(ns);
-    long long eo = 0;
-    for (int i = 0; i < ns; ++i) {
-        eoff[i] = eo;
-        eo += m[i];
+    {
+        long long eo = 0;
+        for (int i = 0; i < ns; ++i) { eoff[i] = eo; eo += m[i]; }
+    }
+    std::vector<int> order(ns);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return m[a] > m[b]; });
+    cudaEvent_t e_rho;
+    GBD_CHECK_CUDA(cudaEventCreateWithFlags(&e_rho, cudaEventDisableTiming));
+    GBD_CHECK_CUDA(cudaEventRecord(e_rho, s));
+    int lw_need[Ctx::kEigStreams] = {0};
+    for (int j = 0; j < ns; ++j) {
+        const int i = order[j], k = j % Ctx::kEigStreams;
         if (m[i] == 0) continue;
         int lw = 0;
-        cusolverDnDsyevd_bufferSize(C.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i],
-                                    rho.as<double>() + roff[i], m[i], evals.as<double>() + eoff[i], &lw);
-        if (lw > lmax) { work.ensure(size_t(lw) * sizeof(double)); lmax = lw; }
-        if (cusolverDnDsyevd(C.sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i], rho.as<double>() + roff[i],
-                             m[i], evals.as<double>() + eoff[i], work.as<double>(), lmax,
-                             info.as<int>() + i) != CUSOLVER_STATUS_SUCCESS)
+        if (cusolverDnDsyevd_bufferSize(C.eig_sol[k], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i],
+                                        rho.as<double>() + roff[i], m[i], evals.as<double>() + eoff[i],
+                                        &lw) != CUSOLVER_STATUS_SUCCESS)
+            throw Error(GBD_ERR_CUDA, "syevd buffer size query failed");
+        lw_need[k] = std::max(lw_need[k], lw);
+    }
+    for (int k = 0; k < Ctx::kEigStreams; ++k) {
+        if (size_t(lw_need[k]) * sizeof(double) > C.eig_work[k].bytes) C.eig_work[k].ensure(size_t(std::max(lw_need[k], 1)) * sizeof(double));
+        GBD_CHECK_CUDA(cudaStreamWaitEvent(C.eig_st[k], e_rho, 0));
+    }
+    for (int j = 0; j < ns; ++j) {
+        const int i = order[j], k = j % Ctx::kEigStreams;
+        if (m[i] == 0) continue;
+        if (cusolverDnDsyevd(C.eig_sol[k], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i],
+                             rho.as<double>() + roff[i], m[i], evals.as<double>() + eoff[i], C.eig_work[k].as<double>(),
+                             lw_need[k], info.as<int>() + i) != CUSOLVER_STATUS_SUCCESS)
             throw Error(GBD_ERR_CUDA, "syevd failed");
     }
+    for (int k = 0; k < Ctx::kEigStreams; ++k) {
+        cudaEvent_t e;
+        GBD_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        GBD_CHECK_CUDA(cudaEventRecord(e, C.eig_st[k]));
+        GBD_CHECK_CUDA(cudaStreamWaitEvent(s, e, 0));
+        cudaEventDestroy(e);
+    }
+    cudaEventDestroy(e_rho);
     std::vector<double> ev(size_t(std::max<long long>(etot, 1)));
     std::vector<int> hinfo(ns + 1);
     GBD_CHECK_CUDA(cudaMemcpyAsync(ev.data(), evals.p, size_t(etot) * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -84,6 +84,10 @@ struct Ctx {
     std::vector<HostEnv> hostL, hostR;
     cudaStream_t cs = nullptr, ios = nullptr;
     cusolverDnHandle_t sol = nullptr;
+    static constexpr int kEigStreams = 4;
+    cudaStream_t eig_st[kEigStreams] = {nullptr};
+    cusolverDnHandle_t eig_sol[kEigStreams] = {nullptr};
+    DevBuf eig_work[kEigStreams];
     Heff H;
     DevBuf psi;
     bool psi_valid = false;
