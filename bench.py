@@ -89,6 +89,29 @@ class Clocks:
         return out
 
 
+def sweep_compare(spec):
+    """Full sweeps from one seeded MPS in FP64 and in the mixed form (sweep wall time, |dE|)."""
+    import inputs
+    import paper_2412_04676_gb300 as g
+    L, N, D, nsw = (int(x) for x in spec.split(","))
+    h, eri = inputs.make_integrals(L, 1000 + L)
+    sites, dims = inputs.make_mps(L, N, 0, D, 77)
+    out = {"workload": f"L={L} N={N} 2Sz=0 D={D}, {nsw} sweeps from the same random MPS"}
+    for name, prec in (("fp64", g.FP64), ("mixed", g.MIXED_BF16X3)):
+        ctx = g.Context(L, N, 0, D=D, precision=prec, offload=True, dav_tol=1e-8)
+        ctx.load_integrals(h, eri)
+        ctx.import_mps(sites, [1] * L)
+        st = ctx.sweep(nsw, D)
+        out[name] = {"ms_per_sweep": [s["ms_total"] for s in st], "energy": st[-1]["energy_last"],
+                     "matvecs": sum(s["matvecs"] for s in st),
+                     "ms_io_exposed": sum(s["ms_io_exposed"] for s in st),
+                     "bytes_packed": sum(s["bytes_packed"] for s in st)}
+        ctx.close()
+    out["abs_dE"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
+    out["speedup_last_sweep"] = out["fp64"]["ms_per_sweep"][-1] / out["mixed"]["ms_per_sweep"][-1]
+    return out
+
+
 # ---------------------------------------------------------------- oracle leg
 def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
     """The oracle's H_eff psi on L=10, N=10, D=256 (mid-chain), timed on host cores.
@@ -167,6 +190,20 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
+def job_times(ms_dev, e2e_ms, world, device):
+    """Slowest replica's device and end-to-end times (max over ranks)."""
+    import torch
+    vals = torch.tensor([ms_dev, e2e_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    return float(vals[0]), float(vals[1])
+
+
+def job_value(world, flops_per_rank, ms):
+    """Whole-job useful TFLOP/s: flops of all replicas over the slowest time."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e12
+
 def run_ours(args, rank, world, local_rank):
     import multiprocessing as mp_
 
@@ -247,19 +284,47 @@ def run_ours(args, rank, world, local_rank):
         h2d += psi.nbytes
         d2h += out.nbytes + 8
         psi = out
+    # pack kernel throughput: HBM -> HBM on the environment the last step
+    # produced, and the offload saves of the timed steps (pinned host memory)
+    pack = None
+    try:
+        side, cut = (0, pos[0]) if dirs[0] == -1 else (1, pos[0] + 2)
+        nbytes = ctx.pack_size(side, cut)
+        io = ctx.io_stats()
+        pk = {"offload_bytes": io["bytes_d2h"], "offload_ms": io["ms_save"],
+              "offload_gbs": io["bytes_d2h"] / (io["ms_save"] * 1e-3) / 1e9 if io["ms_save"] > 0 else None}
+        if nbytes > 0:
+            dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            ctx.pack_env(side, cut, dev)
+            t0 = ctx.io_stats()["ms_pack"]
+            reps = 3
+            for _ in range(reps):
+                ctx.pack_env(side, cut, dev)
+            ms = (ctx.io_stats()["ms_pack"] - t0) / reps
+            gbs = 2 * nbytes / (ms * 1e-3) / 1e9
+            pk.update({"bytes": nbytes, "hbm_ms": ms,
+                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                    "note": "read + write bytes of one packed environment, device to device"}})
+        pack = pk
+    except Exception as e:  # measurement extra; never fatal
+        pack = {"error": repr(e)}
+    sweep = None
+    if args.sweep_config and rank == 0:
+        sweep = sweep_compare(args.sweep_config)
     # the oracle runs only after the GPU measurements, so it never competes for host cores
     if rank == 0 and not args.no_cpu_baseline:
         ctx_mp = mp_.get_context("spawn")
         cpu_q = ctx_mp.Queue()
         cpu_proc = ctx_mp.Process(target=_oracle_child, args=(cpu_q, args.cpu_seconds), daemon=True)
         cpu_proc.start()
-    vals = torch.tensor([ms_dev, e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_dev_max, e2e_max = float(vals[0]), float(vals[1])
-    value = world * flops / (ms_dev_max * 1e-3) / 1e12
-    e2e_value = world * e2e_flops / (e2e_max * 1e-3) / 1e12
+    ms_dev_max, e2e_max = job_times(ms_dev, e2e_ms, world, "cuda")
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    hbm = peaks.get("hbm_gbs", 6787.2)
+    value = job_value(world, flops, ms_dev_max)
+    e2e_value = job_value(world, e2e_flops, e2e_max)
     if rank != 0:
         return 0
     peaks = {}
@@ -323,6 +388,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline_tensor": roof_tc,
         "cpu_baseline": cpu,
         "clocks": clk,
+        "pack": pack,
+        "sweep": sweep,
         "detail": {"matvec_tflops": flops_mv * nmv / (ms_mv * 1e-3) / 1e12 if ms_mv else 0.0, "matvecs": nmv, "ms_matvec": ms_mv, "ms_device": ms_dev,
                    "wall_s": t_wall, "energy": stats[-1]["energy"],
                    "ms_io_exposed": sum(s["ms_io_exposed"] for s in stats),
@@ -351,6 +418,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-matvec", type=int, default=40)
     ap.add_argument("--fp64-peak", type=float, default=1.0975)
+    ap.add_argument("--sweep-config", default="10,10,256,2",
+                    help="L,N,D,sweeps of the FP64-vs-mixed sweep comparison ('' to skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

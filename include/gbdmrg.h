@@ -307,8 +307,12 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
-/* Offload statistics of the context so far. */
-int gbd_io_stats(gbd_ctx* ctx, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack);
+/* Offload statistics of the context so far: bytes saved to / loaded from
+ * pinned host memory, host time blocked on IO events, device time of
+ * gbd_pack_env calls, device time of the asynchronous save kernels (waits
+ * for pending saves to finish).  Any pointer may be NULL. */
+int gbd_io_stats(gbd_ctx* ctx, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack,
+                 double* ms_save);
 
 #ifdef __cplusplus
 }

@@ -100,7 +100,7 @@ _SIGS = {
     "gbd_env_import": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P]),
     "gbd_env_export": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
-                               C.POINTER(C.c_double)]),
+                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gbd_timers": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     "gbd_pack_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, C.c_size_t,
                                    C.POINTER(C.c_size_t), _P]),
@@ -360,6 +360,7 @@ class Context:
         return dict(zip(self.TIMERS, out[:n.value]))
 
     def io_stats(self):
-        v = [C.c_double() for _ in range(4)]
+        v = [C.c_double() for _ in range(5)]
         _check(lib().gbd_io_stats(self.h, *[C.byref(x) for x in v]))
-        return dict(bytes_d2h=v[0].value, bytes_h2d=v[1].value, ms_exposed=v[2].value, ms_pack=v[3].value)
+        return dict(bytes_d2h=v[0].value, bytes_h2d=v[1].value, ms_exposed=v[2].value, ms_pack=v[3].value,
+                    ms_save=v[4].value)

@@ -407,9 +407,12 @@ int gbd_timers(gbd_ctx* c, double* out, int cap, int* n) {
     });
 }
 
-int gbd_io_stats(gbd_ctx* c, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack) {
+int gbd_io_stats(gbd_ctx* c, double* bytes_d2h, double* bytes_h2d, double* ms_exposed, double* ms_pack,
+                 double* ms_save) {
     return guard([&] {
         Ctx& C = ctx(c);
+        if (C.cuda_ready) collect_saves(C, true);
+        if (ms_save) *ms_save = C.save_ms;
         if (bytes_d2h) *bytes_d2h = C.io_d2h;
         if (bytes_h2d) *bytes_h2d = C.io_h2d;
         if (ms_exposed) *ms_exposed = C.io_exposed_ms;

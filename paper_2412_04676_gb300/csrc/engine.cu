@@ -448,8 +448,19 @@ void destroy_ctx(Ctx& C) {
     if (!C.cuda_ready) return;
     cudaSetDevice(C.cfg.device);
     cudaDeviceSynchronize();
-    for (auto& h : C.hostL) { if (h.host) cudaFreeHost(h.host); if (h.done) cudaEventDestroy(h.done); }
-    for (auto& h : C.hostR) { if (h.host) cudaFreeHost(h.host); if (h.done) cudaEventDestroy(h.done); }
+    auto free_host = [](HostEnv& h) {
+        if (h.host) cudaFreeHost(h.host);
+        if (h.meta) cudaFreeHost(h.meta);
+        if (h.cks_host) cudaFreeHost(h.cks_host);
+        if (h.cks_dev) cudaFree(h.cks_dev);
+        if (h.done) cudaEventDestroy(h.done);
+        if (h.loaded) cudaEventDestroy(h.loaded);
+        h = HostEnv();
+    };
+    for (auto& h : C.hostL) free_host(h);
+    for (auto& h : C.hostR) free_host(h);
+    for (auto& ps : C.saves) { cudaEventDestroy(ps.a); cudaEventDestroy(ps.b); }
+    C.saves.clear();
     C.hostL.clear();
     C.hostR.clear();
     if (C.sol) cusolverDnDestroy(C.sol);

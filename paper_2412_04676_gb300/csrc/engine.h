@@ -99,7 +99,9 @@ struct Ctx {
     DevBuf stage;  // device staging for pack/unpack through pageable memory
     // statistics
     std::vector<double> step_energy;
-    double io_d2h = 0, io_h2d = 0, io_exposed_ms = 0, pack_ms = 0;
+    double io_d2h = 0, io_h2d = 0, io_exposed_ms = 0, pack_ms = 0, save_ms = 0;
+    struct PendingSave { cudaEvent_t a, b; };
+    std::vector<PendingSave> saves;   // timing events of asynchronous saves
     double ms_matvec_acc = 0;
     int matvec_count = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -121,6 +123,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);
 double truncate_step(Ctx& C, int dir, int Dmax);
 int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* st);
 void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* st);
+void collect_saves(Ctx& C, bool wait);
 
 // pack / unpack (serialisation)
 size_t pack_size(const OpSet& E);

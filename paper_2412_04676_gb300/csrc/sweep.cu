@@ -325,8 +325,14 @@ void save_async(Ctx& C, int side, int cut) {
     GBD_CHECK_CUDA(cudaEventRecord(ready, C.cs));
     GBD_CHECK_CUDA(cudaStreamWaitEvent(C.ios, ready, 0));
     cudaEventDestroy(ready);
+    Ctx::PendingSave ps{};
+    GBD_CHECK_CUDA(cudaEventCreate(&ps.a));
+    GBD_CHECK_CUDA(cudaEventCreate(&ps.b));
+    GBD_CHECK_CUDA(cudaEventRecord(ps.a, C.ios));
     pack_launch(dev_view<unsigned char>(h.host), nullptr, di, int(P.items.size()), dc, int(P.chunks.size()), h.cks_dev,
                 C.ios);
+    GBD_CHECK_CUDA(cudaEventRecord(ps.b, C.ios));
+    C.saves.push_back(ps);
     GBD_CHECK_CUDA(cudaEventRecord(h.done, C.ios));
     h.valid = true;
     C.io_d2h += double(P.total);
@@ -409,6 +415,24 @@ void ensure_resident(Ctx& C, int side, int cut) {
 
 }  // namespace
 
+// collect the device time of finished asynchronous saves
+void collect_saves(Ctx& C, bool wait) {
+    std::vector<Ctx::PendingSave> keep;
+    for (auto& ps : C.saves) {
+        if (wait) GBD_CHECK_CUDA(cudaEventSynchronize(ps.b));
+        if (cudaEventQuery(ps.b) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ps.a, ps.b);
+            C.save_ms += ms;
+            cudaEventDestroy(ps.a);
+            cudaEventDestroy(ps.b);
+        } else {
+            keep.push_back(ps);
+        }
+    }
+    C.saves.swap(keep);
+}
+
 // ============================================================== step / sweep
 // One DMRG iteration of Sec. II.B at position b, moving towards dir.
 void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
@@ -417,6 +441,7 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     ensure_cuda(C);
     const bool off = C.cfg.offload != 0;
     const int L = C.L;
+    collect_saves(C, false);
     double t0 = now_ms();
     double io0 = C.io_exposed_ms, d2h0 = C.io_d2h, mv0 = C.ms_matvec_acc;
     cudaEvent_t ea, eb;

@@ -76,3 +76,21 @@ def test_mixed_sweep_energy_within_1e6():
         ctx.import_mps(sites, [1] * L)
         out[prec] = ctx.sweep(2, D)[-1]["energy_last"]
     assert abs(out[g.MIXED_BF16X3] - out[g.FP64]) <= 1e-6, out
+
+
+def test_mixed_product_full_size_config2():
+    # L=30, N=30, D=1024 at the mid-chain cut (the bench's launch configuration):
+    # mixed vs the FP64 product of the same library, relative norm error and
+    # the symmetry of the mixed operator (properties that hold at any size)
+    L, N, tsz, D, b = 30, 30, 0, 1024, 14
+    c = heff_case(L, N, tsz, D, 1002, b, oracle=False)
+    ctx = c["ctx"]
+    secs, info = ctx.tables(b)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=info["dim"])
+    z = rng.normal(size=info["dim"])
+    y64 = ctx.apply_heff(b, x, precision=g.FP64)
+    ym = ctx.apply_heff(b, x, precision=g.MIXED_BF16X3)
+    assert np.linalg.norm(ym - y64) <= 2e-5 * np.linalg.norm(y64)
+    zm = ctx.apply_heff(b, z, precision=g.MIXED_BF16X3)
+    assert abs(z @ ym - x @ zm) <= 2e-5 * np.linalg.norm(ym) * np.linalg.norm(z)
