@@ -69,8 +69,9 @@ typedef struct {
     int D;              /* maximum kept states per bond (truncation)            */
     int precision;      /* GBD_FP64 or GBD_MIXED_BF16X3 (H_eff products only)   */
     double dav_tol;     /* Davidson residual norm tolerance (FP64 norm); mixed
-                           precision stops at max(dav_tol, 2e-5), the rounding
-                           floor of its products                             */
+                           precision stops at max(dav_tol, 2e-5) or when the
+                           residual stalls at the rounding floor of its
+                           products (< 10% gain over 8 iterations)           */
     int dav_max_sub;    /* Davidson subspace size before restart                */
     int dav_keep;       /* Ritz vectors kept at restart                         */
     int dav_max_matvec; /* product limit -> GBD_WARN_NOT_CONVERGED              */
