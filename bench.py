@@ -273,10 +273,12 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = 0.0
     e2e_flops = 0.0
     h2d = d2h = 0
+    e2e_stats = []
     for _ in range(args.steps):
         t = time.perf_counter()
         ctx.set_psi(pos[0], host.numpy())
         st = one_step()
+        e2e_stats.append(st)
         out, pb = ctx.get_psi()
         host = torch.from_numpy(out).pin_memory()
         e2e_ms += 1000.0 * (time.perf_counter() - t)
@@ -401,7 +403,9 @@ def run_ours(args, rank, world, local_rank):
                    "bytes_packed_per_step": sum(s["bytes_packed"] for s in stats) / args.steps,
                    "ms_truncate": sum(s["ms_truncate"] for s in stats),
                    "ms_renorm": sum(s["ms_renorm"] for s in stats),
-                   "timers_ms": dt, "ms_fp64_kernels": fp64_ms, "ms_mixed_products": ms_mix}, 
+                   "timers_ms": dt, "ms_fp64_kernels": fp64_ms, "ms_mixed_products": ms_mix,
+                   "steps_matvecs": [s["matvecs"] for s in stats], "e2e_steps_matvecs": [s["matvecs"] for s in e2e_stats],
+                   "e2e_steps_ms": [s["ms_device"] for s in e2e_stats]},
     }
     print(json.dumps(line), flush=True)
     if cpu_proc is not None:
@@ -423,7 +427,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-matvec", type=int, default=40)
     ap.add_argument("--fp64-peak", type=float, default=1.0975)
-    ap.add_argument("--sweep-config", default="10,10,256,2",
+    ap.add_argument("--sweep-config", default="14,14,384,4",
                     help="L,N,D,sweeps of the FP64-vs-mixed sweep comparison ('' to skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -959,7 +959,19 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     }
     scale(V, n, 1.0 / std::sqrt(d[0]), s);
     double ms_mv0 = C.ms_matvec_acc;
-    apply_heff_dev(C, V, AV, prec);
+    // mixed form: the start vector's product is FP64, so the subspace holds
+    // an exact pair from the first iteration (a converged start vector then
+    // costs one FP64 product, as in the FP64 form)
+    // used once the previous solve converged at its first anchor (late sweeps,
+    // good start vectors); far from convergence it would only add an FP64 product
+    const bool exact_start = prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish && C.last_dav_quick;
+    if (exact_start) {
+        const double tp0 = wall_ms();
+        apply_heff_dev(C, V, AV, GBD_FP64);
+        C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
+    } else {
+        apply_heff_dev(C, V, AV, prec);
+    }
     int nmv = 1, k = 1, iters = 0;
     std::vector<double> Hs(size_t(kmax) * kmax, 0.0);
     dots(V, 1, AV, d);
@@ -967,6 +979,8 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     double theta = 0.0, rn = 0.0;
     std::vector<double> w, S;
     std::vector<double> hist;  // residual norms, for the mixed-precision stagnation test
+    int anchors = 0;
+    bool polished = false;
     int status = GBD_OK;
     while (true) {
         ++iters;
@@ -984,16 +998,59 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         axpby(x, r, n, -theta, 1.0, s);
         dots(r, 1, r, d);
         rn = std::sqrt(std::max(0.0, d[0]));
-        if (rn <= tol) break;
-        hist.push_back(rn);
-        if (prec == GBD_MIXED_BF16X3 && hist.size() > 12) {
-            // mixed products carry ~1e-5 relative noise, so the residual stalls
-            // at a floor that grows with |theta|; stop once 8 iterations gave
-            // less than a 10% improvement (the FP64 polish then fixes the energy)
-            const size_t n8 = hist.size() - 8;
-            double before = *std::min_element(hist.begin(), hist.begin() + n8);
-            double recent = *std::min_element(hist.begin() + n8, hist.end());
-            if (recent > 0.9 * before && rn <= 1e-3 * std::max(1.0, std::fabs(theta))) break;
+        bool anchor = false;
+        if (prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish) {
+            // Mixed products carry ~1e-5 relative noise, so the residual stalls
+            // at a floor that grows with |theta|.  At the floor (or at the
+            // tolerance) the Ritz vector is anchored: one FP64 product gives
+            // its exact residual; if that is below the tolerance we are done,
+            // otherwise the subspace restarts from the exact pair and further
+            // mixed directions only correct it, which shrinks the error by
+            // about the products' relative accuracy per round.
+            hist.push_back(rn);
+            bool stalled = false;
+            if (hist.size() > 9) {
+                const size_t n8 = hist.size() - 6;
+                double before = *std::min_element(hist.begin(), hist.begin() + n8);
+                double recent = *std::min_element(hist.begin() + n8, hist.end());
+                stalled = recent > 0.9 * before && rn <= 1e-3 * std::max(1.0, std::fabs(theta));  // < 10% in 6
+            }
+            anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec;
+            if (k == 1 && exact_start && anchors == 0 && iters == 1) {
+                // the residual of the start vector is already exact
+                polished = true;
+                if (rn <= C.cfg.dav_tol) break;
+                anchor = false;
+            }
+        } else if (rn <= tol) {
+            break;
+        }
+        if (anchor) {
+            const double tp0 = wall_ms();
+            apply_heff_dev(C, x, ax, GBD_FP64);
+            C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
+            ++nmv;
+            ++anchors;
+            dots(x, 1, x, d);
+            const double xn = std::sqrt(d[0]);
+            scale(x, n, 1.0 / xn, s);
+            scale(ax, n, 1.0 / xn, s);
+            dots(x, 1, ax, d);
+            theta = d[0];
+            axpby(ax, r, n, 1.0, 0.0, s);
+            axpby(x, r, n, -theta, 1.0, s);
+            dots(r, 1, r, d);
+            rn = std::sqrt(std::max(0.0, d[0]));
+            polished = true;
+            if (rn <= C.cfg.dav_tol || anchors >= 3) break;
+            if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
+            // restart from the exact pair (x, H x)
+            GBD_CHECK_CUDA(cudaMemcpyAsync(V, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            GBD_CHECK_CUDA(cudaMemcpyAsync(AV, ax, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            std::fill(Hs.begin(), Hs.end(), 0.0);
+            Hs[0] = theta;
+            k = 1;
+            hist.clear();
         }
         if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
         precondition(r, H.diag.as<double>(), theta, t, n, s);
@@ -1054,20 +1111,8 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     // normalised Ritz vector becomes the current two-site vector
     dots(x, 1, x, d);
     scale(x, n, 1.0 / std::sqrt(d[0]), s);
-    if (prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish) {
-        // Rayleigh quotient under one FP64 product: the energy error becomes
-        // second order in the mixed-precision product error
-        const double tp0 = wall_ms();
-        apply_heff_dev(C, x, ax, GBD_FP64);
-        C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
-        dots(x, 1, ax, d);
-        theta = d[0];
-        axpby(ax, r, n, 1.0, 0.0, s);
-        axpby(x, r, n, -theta, 1.0, s);
-        dots(r, 1, r, d);
-        rn = std::sqrt(std::max(0.0, d[0]));
-        ++nmv;
-    }
+    (void)polished;
+    if (prec == GBD_MIXED_BF16X3) C.last_dav_quick = (rn <= C.cfg.dav_tol) && anchors <= 1 && status == GBD_OK;
     C.psi.ensure(size_t(n) * sizeof(double));
     GBD_CHECK_CUDA(cudaMemcpyAsync(C.psi.p, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (psi_host) GBD_CHECK_CUDA(cudaMemcpyAsync(psi_host, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s));

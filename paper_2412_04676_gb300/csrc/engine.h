@@ -104,6 +104,7 @@ struct Ctx {
     std::vector<PendingSave> saves;   // timing events of asynchronous saves
     double ms_matvec_acc = 0;
     int matvec_count = 0;
+    bool last_dav_quick = false;  // previous mixed Davidson met its tolerance at the first anchor
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // phase timers (ms): host planning and device execution
     enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_COUNT };
