@@ -79,7 +79,9 @@ typedef struct {
                            creation and unpacked on demand (Sec. III.A)       */
     int device;         /* CUDA device ordinal                                  */
     int switch_cut;     /* cut from which two-operator sets are stored as
-                           complementary sums; 0 = automatic (L/2 + 1)         */
+                           complementary sums; 0 = automatic (L/2 - 1, so the
+                           once-per-half-sweep switch transform is not at the
+                           two central positions)                            */
     int io_timeout_ms;  /* bound on any host wait for an IO event              */
     unsigned long long seed; /* random initial MPS when none is imported       */
     int mixed_fp64_blocks; /* mixed products: the two block Hamiltonian terms
@@ -304,7 +306,8 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
 /* Accumulated phase timers of the context in ms, in this order: enlargement
  * planning (host), enlargement kernels, renormalisation planning (host),
  * renormalisation kernels, per-sector eigensolves, FP64 polish products,
- * mixed-precision operand preparation, Davidson host time (reserved).
+ * mixed-precision operand preparation, Davidson host time (reserved), then
+ * the FP64 GFLOP executed by enlargement and by renormalisation GEMMs.
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

@@ -351,7 +351,7 @@ class Context:
         return out[:n.value]
 
     TIMERS = ["enlarge_host", "enlarge_dev", "renorm_host", "renorm_dev", "eigensolve", "polish", "tc_prepare",
-              "davidson_host"]
+              "davidson_host", "enlarge_gflop", "renorm_gflop"]
 
     def timers(self):
         out = np.zeros(16)

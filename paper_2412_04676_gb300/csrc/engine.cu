@@ -169,21 +169,25 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         }
         links[id].W[size_t(li) * out.cls[co].states.size() + lo] += e.v;
     }
-    // a link whose every output layer has at most one input layer is a set
-    // of scaled copies; the others (complementary sums) are dense GEMMs
+    // a link whose output layers each take few input layers is a set of
+    // scaled copy-sums; the rest (complementary sums over many normal
+    // operators) are dense coefficient GEMMs.  With GB300's narrow FP64 pipe
+    // a dense GEMM over T_in layers costs T_in FMAs per element, a copy-sum
+    // one load per nonzero.
+    constexpr int kMaxCopySources = 32;
     std::vector<char> sparse(links.size(), 1);
-    std::vector<std::vector<std::pair<int, double>>> col_src(links.size());
+    std::vector<std::vector<std::vector<std::pair<int, double>>>> col_src(links.size());
     for (size_t i = 0; i < links.size(); ++i) {
         const int Tin = int(Ein.cls[links[i].ci].states.size());
         const int Tout = int(out.cls[links[i].co].states.size());
         auto& cs = col_src[i];
-        cs.assign(Tout, {-1, 0.0});
+        cs.assign(Tout, {});
         for (int a = 0; a < Tin && sparse[i]; ++a)
             for (int c = 0; c < Tout; ++c) {
                 double v = links[i].W[size_t(a) * Tout + c];
                 if (v == 0.0) continue;
-                if (cs[c].first >= 0) { sparse[i] = 0; break; }
-                cs[c] = {a, v};
+                if ((int)cs[c].size() >= kMaxCopySources) { sparse[i] = 0; break; }
+                cs[c].push_back({a, v});
             }
         if (!sparse[i]) cs.clear();
     }
@@ -263,8 +267,8 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             if (sparse[pr.first]) {
                 const auto& cs = col_src[pr.first];
                 for (int c = 0; c < Tout; ++c)
-                    if (cs[c].first >= 0)
-                        per_layer[c].push_back({din + ib.off + (long long)cs[c].first * ib.rows * ib.cols, cs[c].second});
+                    for (const auto& av : cs[c])
+                        per_layer[c].push_back({din + ib.off + (long long)av.first * ib.rows * ib.cols, av.second});
                 continue;
             }
             GemmSeg g{};
@@ -304,6 +308,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     }
     const double t_dev0 = wall_ms();
     C.timers[Ctx::T_ENL_HOST] += t_dev0 - t_host0;
+    C.timers[Ctx::T_ENL_GFLOP] += P.flops * 1e-9;
     P.upload(C.cs);
     P.launch(C.cs);
     if (!items.empty()) {
@@ -418,6 +423,7 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
     PB.check(bufs, "renormalise/B");
     const double t_dev0 = wall_ms();
     C.timers[Ctx::T_REN_HOST] += t_dev0 - t_host0;
+    C.timers[Ctx::T_REN_GFLOP] += (PA.flops + PB.flops) * 1e-9;
     PA.upload(C.cs);
     PA.launch(C.cs);
     PB.upload(C.cs);
@@ -1013,7 +1019,8 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
                 const size_t n8 = hist.size() - 6;
                 double before = *std::min_element(hist.begin(), hist.begin() + n8);
                 double recent = *std::min_element(hist.begin() + n8, hist.end());
-                stalled = recent > 0.9 * before && rn <= 1e-3 * std::max(1.0, std::fabs(theta));  // < 10% in 6
+                // < 10% gain in 6 iterations, near the mixed floor (~1e-5 |theta|)
+                stalled = recent > 0.9 * before && rn <= 1e-4 * std::max(1.0, std::fabs(theta));
             }
             anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec;
             if (k == 1 && exact_start && anchors == 0 && iters == 1) {

@@ -14,8 +14,8 @@
 // one placed operator or two placed while k < ksw (normal operators of the
 // left block), and S(remaining ops) otherwise (complementary sums: the
 // coefficient is folded in on entering S or F).  ksw moves two-operator
-// sets to the side holding fewer orbitals, which keeps the number of states
-// O(min(k, L-k)^2) per cut.
+// sets to the side holding fewer orbitals (up to a two-cut offset from the
+// centre), which keeps the number of states O(min(k, L-k)^2) per cut.
 #include "mpo.h"
 
 #include <array>
@@ -202,7 +202,12 @@ Q key_dq(Key k) {
 
 void Mpo::build(int L_, const double* h, const double* eri, int ksw_) {
     L = L_;
-    ksw = ksw_ > 0 ? ksw_ : L / 2 + 1;
+    // The switch transform (normal pairs -> complementary pairs, an
+    // O(k^2 (L-k)^2) coefficient contraction at one site) runs once per
+    // half-sweep.  Default: one cut left of the centre, so the centre cut keeps
+    // the minimal operator count and the two central positions do not enlarge
+    // the switch site.
+    ksw = ksw_ > 0 ? ksw_ : std::max(2, L / 2 - 1);
     Builder B;
     B.L = L;
     B.ksw = ksw;

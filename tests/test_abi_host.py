@@ -63,9 +63,14 @@ def test_switch_position_does_not_change_hamiltonian(switch):
 def test_bond_dimension_is_symmetric_and_quadratic():
     L = 12
     h, eri = inputs.make_integrals(L, 5)
-    c = g.Context(L, L, 0)
+    c = g.Context(L, L, 0, switch_cut=L // 2 + 1)
     c.load_integrals(h, eri)
     d = [c.mpo_bond_dim(k) for k in range(L + 1)]
     assert d[0] == 1 and d[L] == 1
     assert d == d[::-1]
     assert max(d) == d[L // 2]
+    # default switch one cut left of the centre: the centre cut is unchanged
+    c2 = g.Context(L, L, 0)
+    c2.load_integrals(h, eri)
+    d2 = [c2.mpo_bond_dim(k) for k in range(L + 1)]
+    assert d2[L // 2] == d[L // 2] and d2[L // 2 + 1:] == d[L // 2 + 1:]
