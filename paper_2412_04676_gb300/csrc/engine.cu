@@ -144,8 +144,11 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     make_classes(M.dq[out_cut], out);
     GBD_REQUIRE(Ein.resident(), GBD_ERR_STATE, "environment not resident on the device");
 
+    // links between an input class and an output class for one local matrix
+    // element (s, t), collected as sparse entries first
     std::map<std::tuple<int, int, int, int>, int> link_id;
     std::vector<Link> links;
+    std::vector<std::vector<std::tuple<int, int, double>>> ents;  // (input layer, output layer, value)
     for (const auto& e : M.W[k]) {
         int sin = side == 0 ? e.a : e.c;
         int sout = side == 0 ? e.c : e.a;
@@ -162,12 +165,12 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             link_id[key] = id;
             Link L;
             L.ci = ci; L.co = co; L.s = e.s; L.t = e.t;
-            L.W.assign(Ein.cls[ci].states.size() * out.cls[co].states.size(), 0.0);
             links.push_back(std::move(L));
+            ents.emplace_back();
         } else {
             id = it->second;
         }
-        links[id].W[size_t(li) * out.cls[co].states.size() + lo] += e.v;
+        ents[id].emplace_back(li, lo, e.v);
     }
     // a link whose output layers each take few input layers is a set of
     // scaled copy-sums; the rest (complementary sums over many normal
@@ -180,16 +183,24 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     for (size_t i = 0; i < links.size(); ++i) {
         const int Tin = int(Ein.cls[links[i].ci].states.size());
         const int Tout = int(out.cls[links[i].co].states.size());
-        auto& cs = col_src[i];
-        cs.assign(Tout, {});
-        for (int a = 0; a < Tin && sparse[i]; ++a)
-            for (int c = 0; c < Tout; ++c) {
-                double v = links[i].W[size_t(a) * Tout + c];
-                if (v == 0.0) continue;
-                if ((int)cs[c].size() >= kMaxCopySources) { sparse[i] = 0; break; }
-                cs[c].push_back({a, v});
+        std::vector<int> cnt(Tout, 0);
+        for (const auto& x : ents[i]) ++cnt[std::get<1>(x)];
+        for (int c = 0; c < Tout; ++c)
+            if (cnt[c] > kMaxCopySources) { sparse[i] = 0; break; }
+        if (sparse[i]) {
+            auto& cs = col_src[i];
+            cs.assign(Tout, {});
+            for (const auto& x : ents[i]) {
+                auto& v = cs[std::get<1>(x)];
+                bool merged = false;
+                for (auto& av : v)
+                    if (av.first == std::get<0>(x)) { av.second += std::get<2>(x); merged = true; }
+                if (!merged) v.push_back({std::get<0>(x), std::get<2>(x)});
             }
-        if (!sparse[i]) cs.clear();
+        } else {
+            links[i].W.assign(size_t(Tin) * Tout, 0.0);
+            for (const auto& x : ents[i]) links[i].W[size_t(std::get<0>(x)) * Tout + std::get<1>(x)] += std::get<2>(x);
+        }
     }
     std::map<std::tuple<int, int, int>, std::vector<int>> by_cst;  // (co, s, t) -> links
     long long wtot = 0;
@@ -259,16 +270,13 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         t.nbatch = 1;
         t.beta = 0.0;
         std::vector<GemmSeg> segs;
-        std::vector<std::vector<CopySrc>> per_layer(Tout);
+        std::vector<std::pair<int, const OpBlock*>> sp;  // sparse links of this sub-block
         for (auto& pr : sub.src) {
             const Link& L = links[pr.first];
             const OpClass& ic = Ein.cls[L.ci];
             const OpBlock& ib = ic.blocks[pr.second];
             if (sparse[pr.first]) {
-                const auto& cs = col_src[pr.first];
-                for (int c = 0; c < Tout; ++c)
-                    for (const auto& av : cs[c])
-                        per_layer[c].push_back({din + ib.off + (long long)av.first * ib.rows * ib.cols, av.second});
+                sp.push_back({pr.first, &ib});
                 continue;
             }
             GemmSeg g{};
@@ -284,16 +292,21 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             segs.push_back(g);
         }
         if (!segs.empty()) P.add_task(t, segs);
+        if (sp.empty()) continue;
         for (int c = 0; c < Tout; ++c) {
-            if (per_layer[c].empty()) continue;
+            const int src0 = int(srcs.size());
+            for (const auto& lb : sp)
+                for (const auto& av : col_src[lb.first][c])
+                    srcs.push_back({din + lb.second->off + (long long)av.first * lb.second->rows * lb.second->cols, av.second});
+            const int nsrc = int(srcs.size()) - src0;
+            if (nsrc == 0) continue;
             CopyItem it{};
             it.dst = dsub + (long long)c * ob.rows * ob.cols;
             it.ldr = ob.cols;
             it.rows = sub.rows;
             it.cols = sub.cols;
-            it.src0 = int(srcs.size());
-            it.nsrc = int(per_layer[c].size());
-            for (auto& x : per_layer[c]) srcs.push_back(x);
+            it.src0 = src0;
+            it.nsrc = nsrc;
             items.push_back(it);
         }
     }
