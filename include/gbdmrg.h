@@ -307,8 +307,10 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * planning (host), enlargement kernels, renormalisation planning (host),
  * renormalisation kernels, per-sector eigensolves, FP64 polish products,
  * mixed-precision operand preparation, Davidson host time (reserved), then
- * the FP64 GFLOP executed by enlargement and by renormalisation GEMMs.
- * *n gets the count; out may be NULL. */
+ * the FP64 GFLOP executed by enlargement and by renormalisation GEMMs, then
+ * the tensor-core GFLOP one mixed product of the last prepared H_eff issues
+ * in phase 1 and in phase 2 (whole tiles, the three split products; not
+ * accumulated).  *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

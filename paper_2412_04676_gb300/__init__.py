@@ -351,7 +351,7 @@ class Context:
         return out[:n.value]
 
     TIMERS = ["enlarge_host", "enlarge_dev", "renorm_host", "renorm_dev", "eigensolve", "polish", "tc_prepare",
-              "davidson_host", "enlarge_gflop", "renorm_gflop"]
+              "davidson_host", "enlarge_gflop", "renorm_gflop", "tc_issued_gflop_p1", "tc_issued_gflop_p2"]
 
     def timers(self):
         out = np.zeros(16)

@@ -107,7 +107,7 @@ struct Ctx {
     bool last_dav_quick = false;  // previous mixed Davidson met its tolerance at the first anchor
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // phase timers (ms): host planning and device execution
-    enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_COUNT };
+    enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2, T_COUNT };
     double timers[T_COUNT] = {0};
 };
 

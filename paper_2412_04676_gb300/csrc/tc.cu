@@ -10,13 +10,16 @@
 // (hi, lo) two-sum pairs, so the long phase-2 reductions do not accumulate
 // FP32 rounding.  Operands reach shared
 // memory through TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
-// three-stage mbarrier pipeline; one thread issues TMA, one issues MMA, eight
-// warps drain TMEM.  Zero fill of TMA boxes handles ragged sector edges.
+// two-stage mbarrier ring; one thread issues TMA, one issues MMA, sixteen
+// warps drain TMEM.  The kernel is persistent (one CTA per SM walking the
+// work list), so loads and MMAs of the next tile overlap the epilogue of the
+// last.  Zero fill of TMA boxes handles ragged sector edges.
 // Every spin-wait is bounded: on expiry the CTA records an error code in a
 // device word, stops issuing, waits (bounded) for its copies and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -29,7 +32,8 @@ namespace tc {
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * BM * (BN * 2 + 16) + 1024;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------ PTX helpers
@@ -132,16 +136,24 @@ __device__ __forceinline__ void locate(const KSeg* segs, int seg0, int nseg, int
 }
 
 // ------------------------------------------------------------------ the kernel
-__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restrict__ works, const KSeg* __restrict__ segs,
+// Persistent: CTA c handles work items c, c + gridDim.x, ...  The TMA
+// producer runs ahead across items through the stage ring, the MMA issuer
+// alternates two TMEM accumulators (a new one per item and per promotion),
+// and the epilogue warps drain one while the MMA fills the other, so the
+// epilogue of one tile overlaps the loads and MMAs of the next.
+constexpr int EPI_RS = BN * 2 + 16;                 // padded row stride of the BF16 staging tile
+constexpr int EPI_BYTES = 2 * BM * EPI_RS;          // hi + lo staging
+
+__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restrict__ works, int nworks,
+                                                             const KSeg* __restrict__ segs,
                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const Work w = works[blockIdx.x];
+    uint8_t* epi = smem + STAGES * STAGE_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = w.c1 - w.c0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
-            mbar_init(smem_u32(&tempty[b]), 8);
+            mbar_init(smem_u32(&tempty[b]), EPI_WARPS);
         }
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -165,92 +177,101 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
-    const int promote = w.promote > 0 ? w.promote : (1 << 30);
-    const int ndrain = n > 0 ? (n + promote - 1) / promote : 0;
 
-    if (warp == 0 && lane == 0 && n > 0) {
+    if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        int s, t, j0;
-        locate(segs, w.seg0, w.nseg, w.c0, s, t, j0);
-        int issued = 0;
-        for (int i = 0; i < n; ++i) {
-            const int st = i % STAGES;
-            if (i >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), ((i / STAGES) & 1) ^ 1)) {
-                atomicExch(err, 1);
-                abort_s = 1;
-                break;
-            }
-            if (abort_s) break;
-            const KSeg sg = segs[s];
-            const uint32_t bar = smem_u32(&full_bar[st]);
-            uint8_t* base = smem + st * STAGE_BYTES;
-            mbar_expect_tx(bar, STAGE_BYTES);
-            const CUtensorMap* mA = maps + sg.mapA;
-            const CUtensorMap* mB = maps + sg.mapB;
-            if (sg.rank == 3) {
-                tma_3d(smem_u32(base), mA, j0, sg.a_row + w.m0, t, bar);
-                tma_3d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, t, bar);
-                tma_3d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, t, bar);
-                tma_3d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, t, bar);
-            } else {
-                tma_2d(smem_u32(base), mA, j0, sg.a_row + w.m0, bar);
-                tma_2d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, bar);
-                tma_2d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, bar);
-                tma_2d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, bar);
-            }
-            ++issued;
-            j0 += BK;
-            if (j0 >= sg.K) {
-                j0 = 0;
-                if (++t >= sg.T) { t = 0; ++s; }
-            }
-        }
-        // on abort: let the loads already issued land before the CTA may exit
-        for (int i = (issued > STAGES ? issued - STAGES : 0); abort_s && i < issued; ++i)
-            mbar_wait(smem_u32(&full_bar[i % STAGES]), (i / STAGES) & 1);
-    } else if (warp == 1 && lane == 0 && n > 0) {
-        // ---------------- MMA issuer
-        int buf = 0, inbuf = 0;
-        int fill0 = 0, fill1 = 0;  // completed fills of each accumulator buffer
-        for (int i = 0; i < n; ++i) {
-            const int st = i % STAGES;
-            if (!mbar_wait(smem_u32(&full_bar[st]), (i / STAGES) & 1)) {
-                atomicExch(err, 2);
-                abort_s = 1;
-                break;
-            }
-            if (abort_s) break;
-            tc_fence_after();
-            const int fills = buf ? fill1 : fill0;
-            if (inbuf == 0 && fills > 0) {
-                if (!mbar_wait(smem_u32(&tempty[buf]), (fills - 1) & 1)) {
-                    atomicExch(err, 3);
+        long long g = 0;  // chunks issued by this CTA
+        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+            const Work w = works[wi];
+            const int n = w.c1 - w.c0;
+            if (n <= 0) continue;
+            int s, t, j0;
+            locate(segs, w.seg0, w.nseg, w.c0, s, t, j0);
+            for (int i = 0; i < n; ++i, ++g) {
+                const int st = int(g % STAGES);
+                if (g >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), uint32_t(((g / STAGES) & 1) ^ 1))) {
+                    atomicExch(err, 1);
                     abort_s = 1;
                     break;
                 }
+                if (abort_s) break;
+                const KSeg sg = segs[s];
+                const uint32_t bar = smem_u32(&full_bar[st]);
+                uint8_t* base = smem + st * STAGE_BYTES;
+                mbar_expect_tx(bar, STAGE_BYTES);
+                const CUtensorMap* mA = maps + sg.mapA;
+                const CUtensorMap* mB = maps + sg.mapB;
+                if (sg.rank == 3) {
+                    tma_3d(smem_u32(base), mA, j0, sg.a_row + w.m0, t, bar);
+                    tma_3d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, t, bar);
+                    tma_3d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, t, bar);
+                    tma_3d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, t, bar);
+                } else {
+                    tma_2d(smem_u32(base), mA, j0, sg.a_row + w.m0, bar);
+                    tma_2d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, bar);
+                    tma_2d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, bar);
+                    tma_2d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, bar);
+                }
+                j0 += BK;
+                if (j0 >= sg.K) {
+                    j0 = 0;
+                    if (++t >= sg.T) { t = 0; ++s; }
+                }
+            }
+        }
+        // on abort: let the loads already issued land before the CTA may exit
+        if (abort_s)
+            for (long long i = (g > STAGES ? g - STAGES : 0); i < g; ++i)
+                mbar_wait(smem_u32(&full_bar[i % STAGES]), uint32_t((i / STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        long long g = 0;   // chunks consumed
+        int D = 0;         // accumulator fills started (buffer D & 1)
+        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+            const Work w = works[wi];
+            const int n = w.c1 - w.c0;
+            if (n <= 0) continue;
+            const int promote = w.promote > 0 ? w.promote : (1 << 30);
+            int inbuf = 0;
+            for (int i = 0; i < n; ++i, ++g) {
+                const int st = int(g % STAGES);
+                if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / STAGES) & 1))) {
+                    atomicExch(err, 2);
+                    abort_s = 1;
+                    break;
+                }
+                if (abort_s) break;
                 tc_fence_after();
-            }
-            const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t a_lo = a_hi + A_BYTES;
-            const uint32_t b_hi = a_hi + 2 * A_BYTES;
-            const uint32_t b_lo = b_hi + B_BYTES;
-            const uint32_t d = tmem + uint32_t(buf * BN);
+                const int buf = D & 1;
+                if (inbuf == 0 && (D >> 1) > 0) {
+                    if (!mbar_wait(smem_u32(&tempty[buf]), uint32_t(((D >> 1) - 1) & 1))) {
+                        atomicExch(err, 3);
+                        abort_s = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
+                const uint32_t a_lo = a_hi + A_BYTES;
+                const uint32_t b_hi = a_hi + 2 * A_BYTES;
+                const uint32_t b_lo = b_hi + B_BYTES;
+                const uint32_t d = tmem + uint32_t(buf * BN);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
-                const uint64_t dah = sdesc(a_hi + off), dal = sdesc(a_lo + off);
-                const uint64_t dbh = sdesc(b_hi + off), dbl = sdesc(b_lo + off);
-                umma(d, dah, dbh, (inbuf > 0 || k > 0) ? 1u : 0u);
-                umma(d, dah, dbl, 1u);
-                umma(d, dal, dbh, 1u);
-            }
-            umma_commit(smem_u32(&empty_bar[st]));
-            ++inbuf;
-            if (inbuf == promote || i == n - 1) {
-                umma_commit(smem_u32(&tfull[buf]));
-                if (buf) ++fill1; else ++fill0;
-                buf ^= 1;
-                inbuf = 0;
+                for (int k = 0; k < BK / 16; ++k) {
+                    const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
+                    const uint64_t dah = sdesc(a_hi + off), dal = sdesc(a_lo + off);
+                    const uint64_t dbh = sdesc(b_hi + off), dbl = sdesc(b_lo + off);
+                    umma(d, dah, dbh, (inbuf > 0 || k > 0) ? 1u : 0u);
+                    umma(d, dah, dbl, 1u);
+                    umma(d, dal, dbh, 1u);
+                }
+                umma_commit(smem_u32(&empty_bar[st]));
+                ++inbuf;
+                if (inbuf == promote || i == n - 1) {
+                    umma_commit(smem_u32(&tfull[buf]));
+                    ++D;
+                    inbuf = 0;
+                }
             }
         }
     } else if (warp >= 2) {
@@ -259,87 +280,97 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         // sum is an error-free FP32 two-sum into a (hi, lo) pair (about 48
         // significant bits); FP64 appears only in the split-K reduction.
         const int quad = warp & 3;          // TMEM lane quadrant this warp may access
-        const int half = (warp - 2) >> 2;   // column half
+        const int part = (warp - 2) >> 2;   // column slice of CP columns
         const int row = quad * 32 + lane;
-        float ah[BN / 2], al[BN / 2];
+        int D = 0;
+        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+            int ndrain;
+            {
+                const int n = works[wi].c1 - works[wi].c0;
+                const int promote = works[wi].promote > 0 ? works[wi].promote : (1 << 30);
+                ndrain = n > 0 ? (n + promote - 1) / promote : 0;
+            }
+            float ah[CP], al[CP];
 #pragma unroll
-        for (int i = 0; i < BN / 2; ++i) { ah[i] = 0.f; al[i] = 0.f; }
-        for (int dd = 0; dd < ndrain; ++dd) {
-            const int buf = dd & 1;
-            bool ok = mbar_wait(smem_u32(&tfull[buf]), (dd >> 1) & 1);
-            if (!ok) { atomicExch(err, 4); abort_s = 1; break; }
-            tc_fence_after();
+            for (int i = 0; i < CP; ++i) { ah[i] = 0.f; al[i] = 0.f; }
+            for (int dd = 0; dd < ndrain; ++dd, ++D) {
+                const int buf = D & 1;
+                if (!mbar_wait(smem_u32(&tfull[buf]), uint32_t((D >> 1) & 1))) { atomicExch(err, 4); abort_s = 1; break; }
+                tc_fence_after();
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t r[16];
-                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + half * (BN / 2) + c * 16);
-                tmem_ld16(taddr, r);
+                for (int c = 0; c < CP / 16; ++c) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + part * CP + c * 16);
+                    tmem_ld16(taddr, r);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float x = __uint_as_float(r[i]);
-                    const float a = ah[c * 16 + i];
-                    const float sum = a + x;
-                    const float bb = sum - a;
-                    al[c * 16 + i] += (a - (sum - bb)) + (x - bb);
-                    ah[c * 16 + i] = sum;
+                    for (int i = 0; i < 16; ++i) {
+                        const float x = __uint_as_float(r[i]);
+                        const float a = ah[c * 16 + i];
+                        const float sum = a + x;
+                        const float bb = sum - a;
+                        al[c * 16 + i] += (a - (sum - bb)) + (x - bb);
+                        ah[c * 16 + i] = sum;
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
-        }
-        const int gr = w.m0 + row;
-        const int gc0 = w.n0 + half * (BN / 2);
-        if (w.out_kind == 0) {
-            // partial tile of (hi, lo) pairs, column-pair-major: a warp writes
-            // 512 contiguous bytes per store
-            float4* out = reinterpret_cast<float4*>(w.out_hi);
+            if (abort_s) break;
+            const Work w = works[wi];  // loaded after the drains: keeps registers free for ah / al
+            const int gr = w.m0 + row;
+            const int gc0 = w.n0 + part * CP;
+            if (w.out_kind == 0) {
+                // partial tile of (hi, lo) pairs, column-pair-major: a warp
+                // writes 512 contiguous bytes per store
+                float4* out = reinterpret_cast<float4*>(w.out_hi);
 #pragma unroll
-            for (int i = 0; i < BN / 2; i += 2)
-                out[(long long)(half * (BN / 4) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
-        } else if (w.out_kind == 1) {
-            // BF16 hi / lo through shared memory (the pipeline stages are idle
-            // now), then coalesced 16-byte stores of whole rows
-            constexpr int RS = BN * 2 + 16;  // padded row stride in bytes
-            uint8_t* sh = smem;
-            uint8_t* sl = smem + BM * RS;
+                for (int i = 0; i < CP; i += 2)
+                    out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
+            } else if (w.out_kind == 1) {
+                // BF16 hi / lo through the staging tile, then coalesced
+                // 16-byte stores of whole rows
+                uint8_t* sh = epi;
+                uint8_t* sl = epi + BM * EPI_RS;
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // previous item's readers are done
 #pragma unroll
-            for (int i = 0; i < BN / 2; i += 8) {
-                uint32_t ph[4], pl[4];
+                for (int i = 0; i < CP; i += 8) {
+                    uint32_t ph[4], pl[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    // x - bf16(x) is exact in FP32, so the split needs no FP64
-                    const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-                    ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
-                    pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+                    for (int k = 0; k < 4; ++k) {
+                        // x - bf16(x) is exact in FP32, so the split needs no FP64
+                        const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                        ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+                        pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+                    }
+                    const int cb = (part * CP + i) * 2;
+                    *reinterpret_cast<uint4*>(sh + row * EPI_RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                    *reinterpret_cast<uint4*>(sl + row * EPI_RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                 }
-                const int cb = (half * (BN / 2) + i) * 2;
-                *reinterpret_cast<uint4*>(sh + row * RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                *reinterpret_cast<uint4*>(sl + row * RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            }
-            asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
-            const int et = threadIdx.x - 64;                  // 0..255
-            const int vpr = BN / 8;                           // 16-byte vectors per row
-            const long long ldo = w.ldo;
-            for (int v = et; v < BM * vpr; v += 256) {
-                const int r = v / vpr, c8 = (v % vpr) * 8;
-                const int grow = w.m0 + r, gcol = w.n0 + c8;
-                if (grow >= w.M || gcol >= ldo) continue;
-                const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * RS + c8 * 2);
-                const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * RS + c8 * 2);
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_hi) + grow * ldo + gcol) = hv;
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_lo) + grow * ldo + gcol) = lv;
-            }
-        } else {
-            if (gr < w.M) {
-                double* o = reinterpret_cast<double*>(w.out_hi) + (long long)gr * w.ldo;
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // all epilogue warps
+                const int et = threadIdx.x - 64;                  // 0 .. EPI_THREADS - 1
+                const int vpr = BN / 8;                           // 16-byte vectors per row
+                const long long ldo = w.ldo;
+                for (int v = et; v < BM * vpr; v += EPI_THREADS) {
+                    const int r = v / vpr, c8 = (v % vpr) * 8;
+                    const int grow = w.m0 + r, gcol = w.n0 + c8;
+                    if (grow >= w.M || gcol >= ldo) continue;
+                    const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * EPI_RS + c8 * 2);
+                    const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * EPI_RS + c8 * 2);
+                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_hi) + grow * ldo + gcol) = hv;
+                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_lo) + grow * ldo + gcol) = lv;
+                }
+            } else {
+                if (gr < w.M) {
+                    double* o = reinterpret_cast<double*>(w.out_hi) + (long long)gr * w.ldo;
 #pragma unroll
-                for (int i = 0; i < BN / 2; ++i)
-                    if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
+                    for (int i = 0; i < CP; ++i)
+                        if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
+                }
             }
         }
     }
@@ -717,6 +748,19 @@ void tc_prepare(Ctx& C) {
     }
     T.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * BN * sizeof(float2));
     for (auto& w : w2) w.out_hi = T.partial.as<float2>() + reinterpret_cast<long long>(w.out_hi) * BM * BN;
+    // tensor-core work issued per product (three split MMAs per K step,
+    // whole 128 x 128 x 64 tiles): the gap to the useful flops is padding
+    auto issued = [](const std::vector<Work>& ws) {
+        double f = 0.0;
+        for (const auto& w : ws) f += double(w.c1 - w.c0) * BM * BN * BK * 2.0 * 3.0;
+        return f * 1e-9;
+    };
+    C.timers[Ctx::T_TC_ISSUE1] = issued(w1);
+    C.timers[Ctx::T_TC_ISSUE2] = issued(w2);
+    // persistent CTAs take items round-robin: longest first evens out the tail
+    auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
+    std::stable_sort(w1.begin(), w1.end(), longer);
+    std::stable_sort(w2.begin(), w2.end(), longer);
     // ---- upload
     T.maps.ensure(std::max<size_t>(maps.size(), 1) * sizeof(CUtensorMap));
     GBD_CHECK_CUDA(cudaMemcpyAsync(T.maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
@@ -735,6 +779,12 @@ void tc_prepare(Ctx& C) {
     T.n_w2 = int(w2.size());
     T.n_red = int(red.size());
     GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    {
+        int dev = 0;
+        GBD_CHECK_CUDA(cudaGetDevice(&dev));
+        GBD_CHECK_CUDA(cudaDeviceGetAttribute(&T.n_sm, cudaDevAttrMultiProcessorCount, dev));
+        T.n_sm = std::max(T.n_sm, 1);
+    }
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));
     T.built = true;
     H.tc_ready = true;
@@ -751,14 +801,14 @@ void tc_apply(Ctx& C) {
         count_launch();
     }
     if (T.n_w1 > 0) {
-        tc_gemm_kernel<<<T.n_w1, THREADS, SMEM_BYTES, st>>>(T.w1.as<Work>(), T.s1.as<KSeg>(), T.maps.as<CUtensorMap>(),
-                                                           T.err.as<int>());
+        tc_gemm_kernel<<<std::min(T.n_w1, T.n_sm), THREADS, SMEM_BYTES, st>>>(
+            T.w1.as<Work>(), T.n_w1, T.s1.as<KSeg>(), T.maps.as<CUtensorMap>(), T.err.as<int>());
         count_launch();
     }
     if (T.n_red > 0) {
         if (T.n_w2 > 0) {
-            tc_gemm_kernel<<<T.n_w2, THREADS, SMEM_BYTES, st>>>(T.w2.as<Work>(), T.s2.as<KSeg>(), T.maps.as<CUtensorMap>(),
-                                                               T.err.as<int>());
+            tc_gemm_kernel<<<std::min(T.n_w2, T.n_sm), THREADS, SMEM_BYTES, st>>>(
+                T.w2.as<Work>(), T.n_w2, T.s2.as<KSeg>(), T.maps.as<CUtensorMap>(), T.err.as<int>());
             count_launch();
         }
         reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<float2>());

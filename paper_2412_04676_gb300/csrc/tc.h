@@ -19,8 +19,11 @@ namespace tc {
 constexpr int BM = 128;       // tile rows (UMMA M)
 constexpr int BN = 128;       // tile cols (UMMA N)
 constexpr int BK = 64;        // K elements per pipeline stage (one 128-byte swizzle row)
-constexpr int STAGES = 3;
-constexpr int THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int STAGES = 2;
+constexpr int EPI_WARPS = 16;                // four per TMEM lane quadrant
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int CP = BN / (EPI_WARPS / 4);     // accumulator columns per epilogue thread
+constexpr int THREADS = 64 + EPI_THREADS;    // warp 0 TMA, warp 1 MMA, then the epilogue warps
 constexpr int TMEM_COLS = 2 * BN;
 
 // One K segment: chunks over layers t < T and inner offsets j0 < K step BK.
@@ -63,7 +66,7 @@ struct TcHeff {
     DevBuf maps;                            // CUtensorMap array (64-byte aligned entries)
     DevBuf w1, s1, w2, s2, red, partial;    // work lists, segments, reductions, split-K partials
     DevBuf err;                             // device error word
-    int n_w1 = 0, n_w2 = 0, n_red = 0;
+    int n_w1 = 0, n_w2 = 0, n_red = 0, n_sm = 152;
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
     std::vector<PsiSec> psec;
