@@ -58,7 +58,17 @@ enum {
     GBD_WARN_NOT_CONVERGED = 1 /* Davidson hit its product limit                 */
 };
 
-enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1 };
+/* H_eff product forms.  GBD_FP64: FP64 GEMMs.  GBD_MIXED_BF16X3: every
+ * operand split elementwise into BF16 hi + lo, products hh + hl + lh on the
+ * tensor cores with FP32 accumulation (~1e-5 relative).  GBD_SLICED_BF16:
+ * every operand row cut into 64-wide blocks, each written exactly as four
+ * BF16 slices on the power-of-two grid of the block maximum (the error-free
+ * splitting of Ozaki et al.); the ten slice products of orders <= 4 run on the
+ * tensor cores, the two leading orders accumulating exactly in FP32 (about
+ * 2^-30 relative to the row maxima).  GBD_SLICED_BF16 is a product form for
+ * gbd_apply_heff and for Davidson anchors (mixed_polish = 2), not a
+ * context precision. */
+enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2 };
 
 typedef struct gbd_ctx gbd_ctx;
 
@@ -86,8 +96,12 @@ typedef struct {
     unsigned long long seed; /* random initial MPS when none is imported       */
     int mixed_fp64_blocks; /* mixed products: the two block Hamiltonian terms
                               (H_left x 1, 1 x H_right) run in FP64           */
-    int mixed_polish;   /* mixed Davidson: the reported energy is the Rayleigh
-                           quotient of the final vector under one FP64 product */
+    int mixed_polish;   /* mixed Davidson anchors: at the tolerance or at the
+                           rounding floor the Ritz vector gets an accurate
+                           product; its Rayleigh quotient and residual decide
+                           convergence, else the subspace restarts from it.
+                           0: none (energy from mixed products), 1: FP64
+                           products, 2: GBD_SLICED_BF16 products            */
 } gbd_config;
 
 typedef struct {
@@ -196,7 +210,8 @@ int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n,
 /* psi_out = H_eff psi_in at position b (Sec. II.B step 2).  Vectors in the
  * sector-major layout above, FP64.  on_device = 1: both pointers are device
  * pointers; 0: host pointers (copied in and out).  precision selects the
- * FP64 or BF16x3 product.  psi_out may not alias psi_in. */
+ * product form (GBD_FP64, GBD_MIXED_BF16X3 or GBD_SLICED_BF16).  psi_out may
+ * not alias psi_in. */
 int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, int on_device, int precision);
 
 /* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
@@ -308,9 +323,15 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * renormalisation kernels, per-sector eigensolves, FP64 polish products,
  * mixed-precision operand preparation, Davidson host time (reserved), then
  * the FP64 GFLOP executed by enlargement and by renormalisation GEMMs, then
- * the tensor-core GFLOP one mixed product of the last prepared H_eff issues
+ * the tensor-core GFLOP one BF16x3 product of the last prepared H_eff issues
  * in phase 1 and in phase 2 (whole tiles, the three split products; not
- * accumulated).  *n gets the count; out may be NULL. */
+ * accumulated), then the device time (ms) of all H_eff products in the
+ * forms GBD_FP64, GBD_MIXED_BF16X3, GBD_SLICED_BF16, then the number of
+ * products in each form, then the tensor-core GFLOP one GBD_SLICED_BF16
+ * product issues (ten slice products; not accumulated), then the host wall
+ * time (ms) of the tensor-core operand preparation in three parts: operator
+ * splitting, planning (work lists, tensor maps), upload.  *n gets the count;
+ * out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
 HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
 
-FP64, MIXED_BF16X3 = 0, 1
+FP64, MIXED_BF16X3, SLICED_BF16 = 0, 1, 2
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
 WARN_NOT_CONVERGED = 1
@@ -199,7 +199,7 @@ class Context:
 
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
-                 mixed_fp64_blocks=True, mixed_polish=True):
+                 mixed_fp64_blocks=True, mixed_polish=2):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -351,12 +351,14 @@ class Context:
         return out[:n.value]
 
     TIMERS = ["enlarge_host", "enlarge_dev", "renorm_host", "renorm_dev", "eigensolve", "polish", "tc_prepare",
-              "davidson_host", "enlarge_gflop", "renorm_gflop", "tc_issued_gflop_p1", "tc_issued_gflop_p2"]
+              "davidson_host", "enlarge_gflop", "renorm_gflop", "tc_issued_gflop_p1", "tc_issued_gflop_p2",
+              "products_fp64_ms", "products_bf16x3_ms", "products_sliced_ms", "products_fp64_n", "products_bf16x3_n",
+              "products_sliced_n", "tc_sliced_issued_gflop", "tc_prep_split", "tc_prep_plan", "tc_prep_upload"]
 
     def timers(self):
-        out = np.zeros(16)
+        out = np.zeros(32)
         n = C.c_int()
-        _check(lib().gbd_timers(self.h, _ptr(out), 16, C.byref(n)))
+        _check(lib().gbd_timers(self.h, _ptr(out), 32, C.byref(n)))
         return dict(zip(self.TIMERS, out[:n.value]))
 
     def io_stats(self):

@@ -62,7 +62,7 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->io_timeout_ms = 120000;
     cfg->seed = 12345;
     cfg->mixed_fp64_blocks = 1;
-    cfg->mixed_polish = 1;
+    cfg->mixed_polish = 2;
     return GBD_OK;
 }
 
@@ -78,6 +78,7 @@ int gbd_create(const gbd_config* cfg, gbd_ctx** out) {
         GBD_REQUIRE(cfg->D >= 1 && cfg->dav_max_sub >= 3 && cfg->dav_max_sub <= 36 && cfg->dav_keep >= 1 &&
                         cfg->dav_max_matvec >= 1 && cfg->dav_tol > 0 && cfg->io_timeout_ms > 0,
                     GBD_ERR_ARG, "bad solver settings");
+        GBD_REQUIRE(cfg->mixed_polish >= 0 && cfg->mixed_polish <= 2, GBD_ERR_ARG, "mixed_polish must be 0, 1 or 2");
         auto* c = new gbd_ctx();
         c->C.cfg = *cfg;
         *out = c;
@@ -179,7 +180,8 @@ int gbd_apply_heff(gbd_ctx* c, int b, const double* psi_in, double* psi_out, int
     return guard([&] {
         Ctx& C = ctx(c);
         GBD_REQUIRE(psi_in && psi_out && psi_in != psi_out, GBD_ERR_ARG, "bad vectors");
-        GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3, GBD_ERR_ARG, "bad precision");
+        GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16, GBD_ERR_ARG,
+                    "bad precision");
         ensure_heff(C, b);
         Heff& H = C.H;
         if (on_device) {

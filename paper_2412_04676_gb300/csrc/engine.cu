@@ -27,11 +27,9 @@
 
 namespace gbd {
 
-namespace {
 double wall_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
-}  // namespace
 
 // ============================================================== bases
 EBasis left_enlarged(const Bond& b) {
@@ -809,14 +807,16 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     Heff& H = C.H;
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
-    if (precision == GBD_MIXED_BF16X3) {
-        if (!H.tc_ready) {
+    const bool tensor = precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16;
+    const int mode = precision == GBD_SLICED_BF16 ? 1 : 0;
+    if (tensor) {
+        if (!H.tc_ready || !H.tc.pl[mode].built) {
             const double tt0 = wall_ms();
-            tc_prepare(C);
+            tc_prepare(C, mode);
             C.timers[Ctx::T_TCPREP] += wall_ms() - tt0;
             GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
         }
-        tc_apply(C);
+        tc_apply(C, mode);
     } else {
         H.p1.launch(C.cs);
         H.p2.launch(C.cs);
@@ -824,7 +824,7 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     GBD_CHECK_CUDA(cudaEventRecord(C.ev1, C.cs));
     GBD_CHECK_CUDA(cudaMemcpyAsync(out, H.yout.p, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventSynchronize(C.ev1));
-    if (precision == GBD_MIXED_BF16X3) {
+    if (tensor) {
         int e = tc_error(C);
         GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core product stopped on a bounded wait (code " + std::to_string(e) + ")");
     }
@@ -832,6 +832,8 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     cudaEventElapsedTime(&ms, C.ev0, C.ev1);
     C.ms_matvec_acc += ms;
     C.matvec_count += 1;
+    C.timers[Ctx::T_PROD_MS0 + precision] += ms;
+    C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
 }
 
 void heff_diag(Ctx& C) {
@@ -984,9 +986,12 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     // used once the previous solve converged at its first anchor (late sweeps,
     // good start vectors); far from convergence it would only add an FP64 product
     const bool exact_start = prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish && C.last_dav_quick;
+    // anchor products: FP64 GEMMs, or the sliced tensor-core form (~2^-30
+    // relative to row maxima, well below the energy tolerance)
+    const int anchor_prec = C.cfg.mixed_polish == 2 ? GBD_SLICED_BF16 : GBD_FP64;
     if (exact_start) {
         const double tp0 = wall_ms();
-        apply_heff_dev(C, V, AV, GBD_FP64);
+        apply_heff_dev(C, V, AV, anchor_prec);
         C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
     } else {
         apply_heff_dev(C, V, AV, prec);
@@ -1047,7 +1052,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         }
         if (anchor) {
             const double tp0 = wall_ms();
-            apply_heff_dev(C, x, ax, GBD_FP64);
+            apply_heff_dev(C, x, ax, anchor_prec);
             C.timers[Ctx::T_POLISH] += wall_ms() - tp0;
             ++nmv;
             ++anchors;

@@ -107,7 +107,9 @@ struct Ctx {
     bool last_dav_quick = false;  // previous mixed Davidson met its tolerance at the first anchor
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // phase timers (ms): host planning and device execution
-    enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2, T_COUNT };
+    enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2,
+           T_PROD_MS0, T_PROD_MS1, T_PROD_MS2, T_PROD_N0, T_PROD_N1, T_PROD_N2, T_TC_ISSUE_SL,
+           T_PREP_SPLIT, T_PREP_PLAN, T_PREP_UPLOAD, T_COUNT };
     double timers[T_COUNT] = {0};
 };
 
@@ -118,6 +120,7 @@ void import_site(Ctx& C, int k, int kind, int nblk, const int* meta, const doubl
 void finalize_sites(Ctx& C);
 void build_envs(Ctx& C, int b);
 void setup_heff(Ctx& C, int b);
+double wall_ms();  // host wall clock in ms
 void apply_heff_dev(Ctx& C, const double* in, double* out, int precision);
 void heff_diag(Ctx& C);
 int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);

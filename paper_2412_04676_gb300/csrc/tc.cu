@@ -1,21 +1,22 @@
-// tc.cu -- mixed-precision H_eff products on the GB300 tensor cores.
+// tc.cu -- H_eff products on the GB300 tensor cores.
 //
 // The product of Sec. II.B step 2 is two grouped GEMM phases over the
 // symmetry sectors (X = O^Lx_stacked psi, then Y += sum_t X_t (O^xR_t)^T with
-// one long K over layers t and inner index j).  Here every operand is split
-// once into BF16 hi + lo (x = hi + lo + O(2^-18 x)) and each tile computes
-// A_hi B_hi + A_hi B_lo + A_lo B_hi with tcgen05.mma (kind::f16, FP32
-// accumulation in TMEM).  The accumulator is promoted to FP64 registers
-// every `promote` K chunks through two ping-pong TMEM buffers into FP32
-// (hi, lo) two-sum pairs, so the long phase-2 reductions do not accumulate
-// FP32 rounding.  Operands reach shared
-// memory through TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
-// two-stage mbarrier ring; one thread issues TMA, one issues MMA, sixteen
-// warps drain TMEM.  The kernel is persistent (one CTA per SM walking the
-// work list), so loads and MMAs of the next tile overlap the epilogue of the
-// last.  Zero fill of TMA boxes handles ragged sector edges.
-// Every spin-wait is bounded: on expiry the CTA records an error code in a
-// device word, stops issuing, waits (bounded) for its copies and frees TMEM.
+// one long K over layers t and inner index j).  Both run here as BF16
+// tcgen05.mma (kind::f16, FP32 accumulation in TMEM) on split operands, in
+// one of two forms (see tc.h): BF16x3 (hi + lo elementwise, three products)
+// for the cheap Davidson products, and four row-scaled slices with ten
+// products for the anchor products.  The TMEM accumulators are promoted into
+// FP32 (hi, lo) two-sum pairs (about 48 significant bits) through two
+// ping-pong buffers, so long phase-2 reductions add no FP32 rounding; FP64
+// appears only in the split-K reduction.  Operands reach shared memory
+// through TMA (cp.async.bulk.tensor, 128-byte swizzle) into a two-stage
+// mbarrier ring; one thread issues TMA, one issues MMA, sixteen warps drain
+// TMEM.  The kernel is persistent (one CTA per SM walking the work list), so
+// loads and MMAs of the next tile overlap the epilogue of the last.  Zero
+// fill of TMA boxes handles ragged sector edges.  Every spin-wait is
+// bounded: on expiry the CTA records an error code in a device word, stops
+// issuing, waits (bounded) for its copies and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -29,12 +30,27 @@
 namespace gbd {
 namespace tc {
 
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * BM * (BN * 2 + 16) + 1024;
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+template <int MODE> struct KT {
+    static constexpr int NS = ModeCfg<MODE>::NS;
+    static constexpr int BN = ModeCfg<MODE>::BN;
+    static constexpr int BUFCOLS = ModeCfg<MODE>::BUFCOLS;
+    static constexpr int TMEM_COLS = ModeCfg<MODE>::TMEM_COLS;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
+    static constexpr int CP = BN / 4;                        // accumulator columns per epilogue thread
+    static constexpr int RS = BN * 2 + 16;                   // padded row stride of a BF16 staging tile
+    static constexpr int EPI_BYTES = (MODE == 0 ? 2 : 1) * BM * RS;  // hi + lo, or one slice at a time
+    static constexpr int RMAX_BYTES = MODE == 1 ? 4 * BM * 4 : 0;    // row maxima of the four column parts
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + RMAX_BYTES + 1024;
+    // instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+    static_assert(CP % 16 == 0, "TMEM loads of 16 columns");
+};
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -78,6 +94,12 @@ __device__ __forceinline__ void tma_3d(uint32_t dst, const void* map, int c0, in
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void tma_4d(uint32_t dst, const void* map, int c0, int c1, int c2, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
@@ -90,13 +112,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return d;
 }
 
-// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
-
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -138,21 +157,29 @@ __device__ __forceinline__ void locate(const KSeg* segs, int seg0, int nseg, int
 // ------------------------------------------------------------------ the kernel
 // Persistent: CTA c handles work items c, c + gridDim.x, ...  The TMA
 // producer runs ahead across items through the stage ring, the MMA issuer
-// alternates two TMEM accumulators (a new one per item and per promotion),
-// and the epilogue warps drain one while the MMA fills the other, so the
-// epilogue of one tile overlaps the loads and MMAs of the next.
-constexpr int EPI_RS = BN * 2 + 16;                 // padded row stride of the BF16 staging tile
-constexpr int EPI_BYTES = 2 * BM * EPI_RS;          // hi + lo staging
+// alternates two TMEM accumulator buffers (a new one per item and per
+// promotion), and the epilogue warps drain one while the MMA fills the other.
 
+// (hi, lo) += x without rounding error (two-sum; hi keeps the FP32 sum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float sum = hi + x;
+    const float bb = sum - hi;
+    lo += (hi - (sum - bb)) + (x - bb);
+    hi = sum;
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restrict__ works, int nworks,
                                                              const KSeg* __restrict__ segs,
                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+    using K_ = KT<MODE>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* epi = smem + STAGES * STAGE_BYTES;
+    uint8_t* epi = smem + STAGES * K_::STAGE_BYTES;
+    float* rmax = reinterpret_cast<float*>(epi + K_::EPI_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -170,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                     "r"(TMEM_COLS)
+                     "r"(K_::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -197,20 +224,22 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 if (abort_s) break;
                 const KSeg sg = segs[s];
                 const uint32_t bar = smem_u32(&full_bar[st]);
-                uint8_t* base = smem + st * STAGE_BYTES;
-                mbar_expect_tx(bar, STAGE_BYTES);
+                uint8_t* base = smem + st * K_::STAGE_BYTES;
+                mbar_expect_tx(bar, K_::STAGE_BYTES);
                 const CUtensorMap* mA = maps + sg.mapA;
                 const CUtensorMap* mB = maps + sg.mapB;
-                if (sg.rank == 3) {
-                    tma_3d(smem_u32(base), mA, j0, sg.a_row + w.m0, t, bar);
-                    tma_3d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, t, bar);
-                    tma_3d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, t, bar);
-                    tma_3d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, t, bar);
-                } else {
-                    tma_2d(smem_u32(base), mA, j0, sg.a_row + w.m0, bar);
-                    tma_2d(smem_u32(base + A_BYTES), mA + 1, j0, sg.a_row + w.m0, bar);
-                    tma_2d(smem_u32(base + 2 * A_BYTES), mB, j0, sg.b_row + w.n0, bar);
-                    tma_2d(smem_u32(base + 2 * A_BYTES + B_BYTES), mB + 1, j0, sg.b_row + w.n0, bar);
+                // the slice planes are the outermost dimension of each map
+#pragma unroll
+                for (int q = 0; q < K_::NS; ++q) {
+                    const uint32_t da = smem_u32(base + q * K_::A_BYTES);
+                    const uint32_t db = smem_u32(base + K_::NS * K_::A_BYTES + q * K_::B_BYTES);
+                    if (sg.rank == 3) {
+                        tma_4d(da, mA, j0, sg.a_row + w.m0, t, q, bar);
+                        tma_4d(db, mB, j0, sg.b_row + w.n0, t, q, bar);
+                    } else {
+                        tma_3d(da, mA, j0, sg.a_row + w.m0, q, bar);
+                        tma_3d(db, mB, j0, sg.b_row + w.n0, q, bar);
+                    }
                 }
                 j0 += BK;
                 if (j0 >= sg.K) {
@@ -251,19 +280,39 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                     }
                     tc_fence_after();
                 }
-                const uint32_t a_hi = smem_u32(smem + st * STAGE_BYTES);
-                const uint32_t a_lo = a_hi + A_BYTES;
-                const uint32_t b_hi = a_hi + 2 * A_BYTES;
-                const uint32_t b_lo = b_hi + B_BYTES;
-                const uint32_t d = tmem + uint32_t(buf * BN);
+                const uint32_t a0 = smem_u32(smem + st * K_::STAGE_BYTES);
+                const uint32_t b0 = a0 + K_::NS * K_::A_BYTES;
+                const uint32_t d = tmem + uint32_t(buf * K_::BUFCOLS);
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k) {
                     const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
-                    const uint64_t dah = sdesc(a_hi + off), dal = sdesc(a_lo + off);
-                    const uint64_t dbh = sdesc(b_hi + off), dbl = sdesc(b_lo + off);
-                    umma(d, dah, dbh, (inbuf > 0 || k > 0) ? 1u : 0u);
-                    umma(d, dah, dbl, 1u);
-                    umma(d, dal, dbh, 1u);
+                    const uint32_t acc = (inbuf > 0 || k > 0) ? 1u : 0u;
+                    if constexpr (MODE == 0) {
+                        const uint64_t ah = sdesc(a0 + off), al = sdesc(a0 + K_::A_BYTES + off);
+                        const uint64_t bh = sdesc(b0 + off), bl = sdesc(b0 + K_::B_BYTES + off);
+                        umma(d, ah, bh, K_::IDESC, acc);
+                        umma(d, ah, bl, K_::IDESC, 1u);
+                        umma(d, al, bh, K_::IDESC, 1u);
+                    } else {
+                        // slice products by order: a1 b1 | a1 b2 + a2 b1 | orders 3 and 4
+                        uint64_t sa[4], sb[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            sa[q] = sdesc(a0 + q * K_::A_BYTES + off);
+                            sb[q] = sdesc(b0 + q * K_::B_BYTES + off);
+                        }
+                        const uint32_t d2 = d + 64, d3 = d + 128;
+                        umma(d, sa[0], sb[0], K_::IDESC, acc);
+                        umma(d2, sa[0], sb[1], K_::IDESC, acc);
+                        umma(d2, sa[1], sb[0], K_::IDESC, 1u);
+                        umma(d3, sa[0], sb[2], K_::IDESC, acc);
+                        umma(d3, sa[1], sb[1], K_::IDESC, 1u);
+                        umma(d3, sa[2], sb[0], K_::IDESC, 1u);
+                        umma(d3, sa[0], sb[3], K_::IDESC, 1u);
+                        umma(d3, sa[1], sb[2], K_::IDESC, 1u);
+                        umma(d3, sa[2], sb[1], K_::IDESC, 1u);
+                        umma(d3, sa[3], sb[0], K_::IDESC, 1u);
+                    }
                 }
                 umma_commit(smem_u32(&empty_bar[st]));
                 ++inbuf;
@@ -276,9 +325,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         }
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> FP32 (hi, lo) pairs
-        // GB300's FP64 pipe is narrow, so the promotion of each TMEM partial
-        // sum is an error-free FP32 two-sum into a (hi, lo) pair (about 48
-        // significant bits); FP64 appears only in the split-K reduction.
+        // GB300's FP64 pipe is narrow, so each promotion is an error-free FP32
+        // two-sum into a (hi, lo) pair (about 48 significant bits).
+        constexpr int CP = K_::CP;
         const int quad = warp & 3;          // TMEM lane quadrant this warp may access
         const int part = (warp - 2) >> 2;   // column slice of CP columns
         const int row = quad * 32 + lane;
@@ -297,19 +346,26 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int buf = D & 1;
                 if (!mbar_wait(smem_u32(&tfull[buf]), uint32_t((D >> 1) & 1))) { atomicExch(err, 4); abort_s = 1; break; }
                 tc_fence_after();
+                const uint32_t tb = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * K_::BUFCOLS + part * CP);
+                if constexpr (MODE == 0) {
 #pragma unroll
-                for (int c = 0; c < CP / 16; ++c) {
-                    uint32_t r[16];
-                    const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * BN + part * CP + c * 16);
-                    tmem_ld16(taddr, r);
+                    for (int c = 0; c < CP / 16; ++c) {
+                        uint32_t r[16];
+                        tmem_ld16(tb + c * 16, r);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) two_sum_acc(ah[c * 16 + i], al[c * 16 + i], __uint_as_float(r[i]));
+                    }
+                } else {
+                    // order 1 and order 2 are exact FP32 sums; orders 3-4 are
+                    // 2^-16 of order 1, so one rounded add joins them to order 2
+                    uint32_t r1[16], r2[16], r3[16];
+                    tmem_ld16(tb, r1);
+                    tmem_ld16(tb + 64, r2);
+                    tmem_ld16(tb + 128, r3);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const float x = __uint_as_float(r[i]);
-                        const float a = ah[c * 16 + i];
-                        const float sum = a + x;
-                        const float bb = sum - a;
-                        al[c * 16 + i] += (a - (sum - bb)) + (x - bb);
-                        ah[c * 16 + i] = sum;
+                        two_sum_acc(ah[i], al[i], __uint_as_float(r1[i]));
+                        two_sum_acc(ah[i], al[i], __uint_as_float(r2[i]) + __uint_as_float(r3[i]));
                     }
                 }
                 tc_fence_before();
@@ -323,50 +379,107 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             if (w.out_kind == 0) {
                 // partial tile of (hi, lo) pairs, column-pair-major: a warp
                 // writes 512 contiguous bytes per store
-                float4* out = reinterpret_cast<float4*>(w.out_hi);
+                float4* out = reinterpret_cast<float4*>(w.out);
 #pragma unroll
                 for (int i = 0; i < CP; i += 2)
                     out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
             } else if (w.out_kind == 1) {
-                // BF16 hi / lo through the staging tile, then coalesced
-                // 16-byte stores of whole rows
-                uint8_t* sh = epi;
-                uint8_t* sl = epi + BM * EPI_RS;
-                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // previous item's readers are done
-#pragma unroll
-                for (int i = 0; i < CP; i += 8) {
-                    uint32_t ph[4], pl[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        // x - bf16(x) is exact in FP32, so the split needs no FP64
-                        const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
-                        const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-                        ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
-                        pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
-                    }
-                    const int cb = (part * CP + i) * 2;
-                    *reinterpret_cast<uint4*>(sh + row * EPI_RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                    *reinterpret_cast<uint4*>(sl + row * EPI_RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-                }
-                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // all epilogue warps
-                const int et = threadIdx.x - 64;                  // 0 .. EPI_THREADS - 1
-                const int vpr = BN / 8;                           // 16-byte vectors per row
+                __nv_bfloat16* o0 = reinterpret_cast<__nv_bfloat16*>(w.out);
                 const long long ldo = w.ldo;
-                for (int v = et; v < BM * vpr; v += EPI_THREADS) {
-                    const int r = v / vpr, c8 = (v % vpr) * 8;
-                    const int grow = w.m0 + r, gcol = w.n0 + c8;
-                    if (grow >= w.M || gcol >= ldo) continue;
-                    const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * EPI_RS + c8 * 2);
-                    const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * EPI_RS + c8 * 2);
-                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_hi) + grow * ldo + gcol) = hv;
-                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(w.out_lo) + grow * ldo + gcol) = lv;
+                const int et = threadIdx.x - 64;  // 0 .. EPI_THREADS - 1
+                constexpr int vpr = K_::BN / 8;   // 16-byte vectors per row
+                if constexpr (MODE == 0) {
+                    // BF16 hi / lo through the staging tile, then coalesced
+                    // 16-byte stores of whole rows
+                    uint8_t* sh = epi;
+                    uint8_t* sl = epi + BM * K_::RS;
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // previous item's readers are done
+#pragma unroll
+                    for (int i = 0; i < CP; i += 8) {
+                        uint32_t ph[4], pl[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            // x - bf16(x) is exact in FP32, so the split needs no FP64
+                            const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
+                            const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+                            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                            ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+                            pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+                        }
+                        const int cb = (part * CP + i) * 2;
+                        *reinterpret_cast<uint4*>(sh + row * K_::RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                        *reinterpret_cast<uint4*>(sl + row * K_::RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // all epilogue warps
+                    for (int v = et; v < BM * vpr; v += EPI_THREADS) {
+                        const int r = v / vpr, c8 = (v % vpr) * 8;
+                        const int grow = w.m0 + r, gcol = w.n0 + c8;
+                        if (grow >= w.M || gcol >= ldo) continue;
+                        const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * K_::RS + c8 * 2);
+                        const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * K_::RS + c8 * 2);
+                        *reinterpret_cast<uint4*>(o0 + grow * ldo + gcol) = hv;
+                        *reinterpret_cast<uint4*>(o0 + w.plane + grow * ldo + gcol) = lv;
+                    }
+                } else {
+                    // four slices on the grid of this row's maximum over the
+                    // tile's 64 columns (the K block of the next phase)
+                    float m = 0.f;
+#pragma unroll
+                    for (int i = 0; i < CP; ++i) m = fmaxf(m, fabsf(ah[i]));
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // previous item's readers are done
+                    rmax[part * BM + row] = m;
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                    m = fmaxf(fmaxf(rmax[row], rmax[BM + row]), fmaxf(rmax[2 * BM + row], rmax[3 * BM + row]));
+                    int ex = 0;
+                    frexpf(m, &ex);  // |x| <= m < 2^ex for every x of the row
+                    uint32_t pk[4][CP / 2];
+#pragma unroll
+                    for (int i = 0; i < CP; i += 2) {
+                        __nv_bfloat16 q0[4], q1[4];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // s_k = round(x 2^(8k - ex)) 2^(ex - 8k) of the remainder;
+                            // each difference is exact, each slice has <= 8 bits
+                            float r = ah[i + h];
+                            const float s1 = ldexpf(rintf(ldexpf(r, 8 - ex)), ex - 8);
+                            r = (r - s1) + al[i + h];
+                            const float s2 = ldexpf(rintf(ldexpf(r, 16 - ex)), ex - 16);
+                            r -= s2;
+                            const float s3 = ldexpf(rintf(ldexpf(r, 24 - ex)), ex - 24);
+                            r -= s3;
+                            const float s4 = ldexpf(rintf(ldexpf(r, 32 - ex)), ex - 32);
+                            __nv_bfloat16* q = h == 0 ? q0 : q1;
+                            q[0] = __float2bfloat16_rn(s1);
+                            q[1] = __float2bfloat16_rn(s2);
+                            q[2] = __float2bfloat16_rn(s3);
+                            q[3] = __float2bfloat16_rn(s4);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            pk[q][i / 2] = uint32_t(__bfloat16_as_ushort(q0[q])) | (uint32_t(__bfloat16_as_ushort(q1[q])) << 16);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q > 0) asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // plane q-1 copied out
+#pragma unroll
+                        for (int i = 0; i < CP / 2; i += 4)
+                            *reinterpret_cast<uint4*>(epi + row * K_::RS + part * CP * 2 + i * 4) =
+                                make_uint4(pk[q][i], pk[q][i + 1], pk[q][i + 2], pk[q][i + 3]);
+                        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                        for (int v = et; v < BM * vpr; v += EPI_THREADS) {
+                            const int r = v / vpr, c8 = (v % vpr) * 8;
+                            const int grow = w.m0 + r, gcol = w.n0 + c8;
+                            if (grow >= w.M || gcol >= ldo) continue;
+                            *reinterpret_cast<uint4*>(o0 + q * w.plane + grow * ldo + gcol) =
+                                *reinterpret_cast<const uint4*>(epi + r * K_::RS + c8 * 2);
+                        }
+                    }
                 }
             } else {
                 if (gr < w.M) {
-                    double* o = reinterpret_cast<double*>(w.out_hi) + (long long)gr * w.ldo;
+                    double* o = reinterpret_cast<double*>(w.out) + (long long)gr * w.ldo;
 #pragma unroll
                     for (int i = 0; i < CP; ++i)
                         if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
@@ -377,45 +490,112 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(K_::TMEM_COLS) : "memory");
     }
 }
 
 // ------------------------------------------------------------------ helpers
-// x = hi + lo with hi = bf16(x), lo = bf16(x - hi); rows padded with zeros
-struct SplitBlock {
+// Operand splitting.  Element (r, c) of the source is src[r * rs + c * cs];
+// columns from cols to ldd - 1 are zero padding; plane k of the output
+// starts at dst + k * plane.  A group of G lanes handles one (row, 64-column
+// block) unit (G = 32, or 8 / 16 for short rows, so a warp then covers
+// several rows).  GB300's FP64 pipe is narrow, so the per-element work is
+// integer and FP32 arithmetic on the FP64 bit patterns.
+//   MODE 0: x = hi + lo, hi = bf16(f), lo = bf16(f - hi) with f = fp32(x)
+//     (|x - hi - lo| <= 2^-18 |x|).
+//   MODE 1: error-free slicing: with 2^(e-1) <= max |x| < 2^e over the unit,
+//     q = round(x 2^(32-e)) (|q| <= 2^32) is cut into balanced base-256
+//     digits q = m1 2^24 + m2 2^16 + m3 2^8 + m4 (|m1| <= 256, |mk| <= 128),
+//     and slice k = mk 2^(e - 8k) is exact in BF16; x = sum of the slices
+//     + O(2^(e-33)).  Units whose maximum is zero or subnormal are zero.
+struct SplitDesc {
     const double* src;
-    __nv_bfloat16* hi;
-    __nv_bfloat16* lo;
+    long long rs, cs;
     long long rows;
     int cols, ldd;
+    __nv_bfloat16* dst;
+    long long plane;
 };
 
-__global__ void split_kernel(const SplitBlock* __restrict__ blocks, int nb) {
-    const SplitBlock b = blocks[blockIdx.y];
-    const long long n = b.rows * b.ldd;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long r = e / b.ldd;
-        const int c = int(e % b.ldd);
-        double x = c < b.cols ? b.src[r * b.cols + c] : 0.0;
-        __nv_bfloat16 h = __float2bfloat16_rn(float(x));
-        b.hi[e] = h;
-        b.lo[e] = __float2bfloat16_rn(float(x - double(__bfloat162float(h))));
-    }
+__device__ __forceinline__ float pow2f(int e) {
+    return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.f, e);
 }
 
-// psi^T per sector: dst[n][k] = psi[k][n], split into hi / lo
-__global__ void split_psi_kernel(const double* __restrict__ psi, const TcHeff::PsiSec* __restrict__ secs,
-                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-    const TcHeff::PsiSec s = secs[blockIdx.y];
-    const long long n = (long long)s.mR * s.ldp;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int r = int(e / s.ldp);  // column of psi
-        const int k = int(e % s.ldp);  // row of psi
-        double x = k < s.mL ? psi[s.src + (long long)k * s.mR + r] : 0.0;
-        __nv_bfloat16 h = __float2bfloat16_rn(float(x));
-        hi[s.dst + e] = h;
-        lo[s.dst + e] = __float2bfloat16_rn(float(x - double(__bfloat162float(h))));
+// One CTA per descriptor; descriptors cover at most kSplitUnits units, so the
+// work spreads over the whole GPU however unequal the operator blocks are.
+constexpr int kSplitUnits = 2048;
+
+template <int MODE>
+__global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
+    const SplitDesc b = blocks[blockIdx.x];
+    const int nb64 = (b.ldd + 63) >> 6;
+    const int G = b.ldd > 16 ? 32 : (b.ldd > 8 ? 16 : 8);
+    const int upw = 32 / G;  // units per warp and iteration
+    const long long units = b.rows * nb64;
+    const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
+    const long long nw = blockDim.x >> 5;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.src);
+    for (long long u0 = (threadIdx.x >> 5) * upw; u0 < units; u0 += nw * upw) {
+        const long long u = u0 + sub;
+        const bool uv = u < units;
+        const long long r = uv ? u / nb64 : 0;
+        const int c0 = uv ? int(u - r * nb64) * 64 : 0;
+        unsigned long long bits[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c0 + gl + G * h;
+            bits[h] = (uv && c < b.cols && c < c0 + 64) ? src[r * b.rs + (long long)c * b.cs] : 0ULL;
+        }
+        __nv_bfloat16* d = b.dst + r * b.ldd;
+        if constexpr (MODE == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + gl + G * h;
+                if (!uv || c >= b.ldd || c >= c0 + 64) continue;
+                const float f = __double2float_rn(__longlong_as_double((long long)bits[h]));
+                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                d[c] = hi;
+                d[b.plane + c] = __float2bfloat16_rn(f - __bfloat162float(hi));
+            }
+        } else {
+            // block maximum: non-negative doubles order like their bit patterns
+            const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFULL;
+            unsigned long long mag = max(bits[0] & kAbs, bits[1] & kAbs);
+            for (int o = G / 2; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, mag, o);
+                mag = max(mag, t);
+            }
+            const int emax = int(mag >> 52);  // biased exponent of the maximum
+            const int ex = emax - 1022;       // max < 2^ex
+            float sc[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + gl + G * h;
+                if (!uv || c >= b.ldd || c >= c0 + 64) continue;
+                const unsigned long long w = bits[h];
+                const int E = int((w >> 52) & 0x7FF);
+                long long q = 0;
+                if (emax > 0 && E > 0) {
+                    // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
+                    const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+                    const int sh = 21 + (emax - E);
+                    q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
+                    if (w >> 63) q = -q;
+                }
+                const long long m1 = (q + (1LL << 23)) >> 24;
+                long long rem = q - (m1 << 24);
+                const long long m2 = (rem + (1LL << 15)) >> 16;
+                rem -= m2 << 16;
+                const long long m3 = (rem + (1LL << 7)) >> 8;
+                const long long m4 = rem - (m3 << 8);
+                d[c] = __float2bfloat16_rn(float(m1) * sc[0]);
+                d[b.plane + c] = __float2bfloat16_rn(float(m2) * sc[1]);
+                d[2 * b.plane + c] = __float2bfloat16_rn(float(m3) * sc[2]);
+                d[3 * b.plane + c] = __float2bfloat16_rn(float(m4) * sc[3]);
+            }
+        }
     }
 }
 
@@ -423,25 +603,17 @@ __global__ void split_psi_kernel(const double* __restrict__ psi, const TcHeff::P
 // at pair index ((j / 2) * BM + i) * 2 + (j % 2)
 __global__ void reduce_kernel(const Reduce* __restrict__ red, const float2* __restrict__ partial) {
     const Reduce r = red[blockIdx.x];
-    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
-        const int i = e / BN, j = e % BN;
+    for (int e = threadIdx.x; e < BM * r.bn; e += blockDim.x) {
+        const int i = e / r.bn, j = e % r.bn;
         const int gi = r.m0 + i, gj = r.n0 + j;
         if (gi >= r.M || gj >= r.N) continue;
         const long long idx = ((long long)(j / 2) * BM + i) * 2 + (j % 2);
         double v = 0.0;
         for (int p = r.p0; p < r.p1; ++p) {
-            const float2 x = partial[(long long)p * BM * BN + idx];
+            const float2 x = partial[(long long)p * BM * r.bn + idx];
             v += double(x.x) + double(x.y);
         }
         r.out[(long long)gi * r.ldo + gj] = v;
-    }
-}
-
-__global__ void zero_rows_kernel(const Reduce* __restrict__ red) {
-    const Reduce r = red[blockIdx.x];
-    for (int e = threadIdx.x; e < BM * BN; e += blockDim.x) {
-        const int gi = r.m0 + e / BN, gj = r.n0 + e % BN;
-        if (gi < r.M && gj < r.N) r.out[(long long)gi * r.ldo + gj] = 0.0;
     }
 }
 
@@ -462,17 +634,34 @@ EncodeTiled encoder() {
     return fn;
 }
 
-// BF16 K-major operand: inner extent K (elements), rows, optional layers; row
-// pitch ld elements (multiple of 8), layer pitch in elements.
-CUtensorMap make_map(const void* base, int K, long long rows, int layers, int ld, long long layer_pitch, int box_rows) {
+// BF16 K-major operand: inner extent K (elements), rows, optional layers,
+// then the slice planes; row pitch ld elements (multiple of 8), layer and
+// plane pitches in elements (multiples of 8).
+CUtensorMap make_map(const void* base, int K, long long rows, int layers, int ld, long long layer_pitch, int planes,
+                     long long plane_pitch, int box_rows) {
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
-    GBD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && ld % 8 == 0, GBD_ERR_STATE, "TMA operand misaligned");
-    cuuint64_t dims[3] = {cuuint64_t(std::max(K, 1)), cuuint64_t(std::max<long long>(rows, 1)), cuuint64_t(std::max(layers, 1))};
-    cuuint64_t strides[2] = {cuuint64_t(ld) * 2, cuuint64_t(layer_pitch) * 2};
-    cuuint32_t box[3] = {cuuint32_t(BK), cuuint32_t(box_rows), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    cuuint32_t rank = layers > 0 ? 3 : 2;
+    GBD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && ld % 8 == 0 && layer_pitch % 8 == 0 &&
+                    plane_pitch % 8 == 0,
+                GBD_ERR_STATE, "TMA operand misaligned");
+    cuuint64_t dims[4];
+    cuuint64_t strides[3];
+    cuuint32_t box[4];
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    cuuint32_t rank = 0;
+    dims[rank] = cuuint64_t(std::max(K, 1));
+    box[rank++] = cuuint32_t(BK);
+    dims[rank] = cuuint64_t(std::max<long long>(rows, 1));
+    strides[rank - 1] = cuuint64_t(ld) * 2;
+    box[rank++] = cuuint32_t(box_rows);
+    if (layers > 0) {
+        dims[rank] = cuuint64_t(layers);
+        strides[rank - 1] = cuuint64_t(layer_pitch) * 2;
+        box[rank++] = 1;
+    }
+    dims[rank] = cuuint64_t(std::max(planes, 1));
+    strides[rank - 1] = cuuint64_t(std::max<long long>(plane_pitch, 8)) * 2;
+    box[rank++] = 1;
     CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -486,140 +675,166 @@ inline int pad8(int x) { return (x + 7) / 8 * 8; }
 
 using namespace tc;
 
-// Builds BF16 operands, tensor maps and work lists for the current position.
-void tc_prepare(Ctx& C) {
+namespace {
+
+// Operator blocks laid out class by class, rows padded to 8 elements.
+long long op_layout(const OpSet& O, std::vector<std::vector<long long>>& off) {
+    long long tot = 0;
+    off.assign(O.cls.size(), {});
+    for (size_t c = 0; c < O.cls.size(); ++c)
+        for (const auto& b : O.cls[c].blocks) {
+            off[c].push_back(tot);
+            tot += (long long)O.cls[c].states.size() * b.rows * pad8(b.cols);
+        }
+    return tot;
+}
+
+template <class T> void upload_vec(DevBuf& d, const std::vector<T>& v, cudaStream_t st) {
+    d.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+    if (!v.empty()) GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+// FP64 path of the two block-Hamiltonian terms (mode 0, optional): their
+// layers are zeroed in the BF16 copies and applied in FP64 after each product.
+void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long long>>& offL,
+                       const std::vector<std::vector<long long>>& offR) {
     Heff& H = C.H;
     TcHeff& T = H.tc;
-    T = TcHeff();
     cudaStream_t st = C.cs;
-    // ---- BF16 operator arenas (hi / lo), rows padded to 8 elements
-    auto layout = [&](const OpSet& O, std::vector<std::vector<long long>>& off) {
-        long long tot = 0;
-        off.assign(O.cls.size(), {});
-        for (size_t c = 0; c < O.cls.size(); ++c)
-            for (const auto& b : O.cls[c].blocks) {
-                off[c].push_back(tot);
-                tot += (long long)O.cls[c].states.size() * b.rows * pad8(b.cols);
-            }
-        return tot;
-    };
-    std::vector<std::vector<long long>> offL, offR;
-    long long nL = layout(H.OL, offL), nR = layout(H.OR, offR);
-    T.ol_hi.ensure(size_t(std::max(nL, 8LL)) * 2);
-    T.ol_lo.ensure(size_t(std::max(nL, 8LL)) * 2);
-    T.or_hi.ensure(size_t(std::max(nR, 8LL)) * 2);
-    T.or_lo.ensure(size_t(std::max(nR, 8LL)) * 2);
-    T.bytes_ops = double(nL + nR) * 4.0;
-    std::vector<SplitBlock> sb;
-    auto add_split = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& hi, DevBuf& lo) {
-        for (size_t c = 0; c < O.cls.size(); ++c)
-            for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
-                const OpBlock& b = O.cls[c].blocks[i];
-                sb.push_back({O.data.as<double>() + b.off, hi.as<__nv_bfloat16>() + off[c][i],
-                              lo.as<__nv_bfloat16>() + off[c][i], (long long)O.cls[c].states.size() * b.rows, b.cols,
-                              pad8(b.cols)});
-            }
-    };
-    add_split(H.OL, offL, T.ol_hi, T.ol_lo);
-    add_split(H.OR, offR, T.or_hi, T.or_lo);
-    if (!sb.empty()) {
-        DevBuf d;
-        d.ensure(sb.size() * sizeof(SplitBlock));
-        GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, sb.data(), sb.size() * sizeof(SplitBlock), cudaMemcpyHostToDevice, st));
-        for (size_t i0 = 0; i0 < sb.size(); i0 += 65535) {
-            unsigned nb = unsigned(std::min<size_t>(65535, sb.size() - i0));
-            split_kernel<<<dim3(32, nb), 256, 0, st>>>(d.as<SplitBlock>() + i0, int(nb));
-            count_launch();
-        }
-        GBD_CHECK_CUDA(cudaGetLastError());
-        GBD_CHECK_CUDA(cudaStreamSynchronize(st));
-    }
-    // ---- optional FP64 path for the two block-Hamiltonian terms: their
-    // layers are zeroed in the BF16 copies and applied in FP64 afterwards
     const int cut = H.b + 1;
     const int sI = C.mpo.idxI[cut], sF = C.mpo.idxF[cut];
     T.blk = C.cfg.mixed_fp64_blocks && sI >= 0 && sF >= 0;
-    if (T.blk) {
-        int c0 = H.OL.state_class[sI];
-        GBD_REQUIRE(c0 == H.OL.state_class[sF], GBD_ERR_STATE, "block terms in different classes");
-        const int Tn = int(H.OL.cls[c0].states.size());
-        const int lay[2] = {H.OL.state_layer[sI], H.OL.state_layer[sF]};
-        std::vector<long long> xoff(H.sq.size() * 2);
-        long long xt = 0;
-        for (size_t q = 0; q < H.sq.size(); ++q)
-            for (int k = 0; k < 2; ++k) {
-                xoff[q * 2 + k] = xt;
-                xt += (long long)H.bL.dim[H.sL[q]] * H.bR.dim[H.sR[q]];
-            }
-        T.blk_x.ensure(size_t(std::max(xt, 1LL)) * 8);
-        T.blk_a.clear();
-        T.blk_b.clear();
-        for (int side = 0; side < 2; ++side) {
-            const OpSet& O = side == 0 ? H.OL : H.OR;
-            DevBuf& hi = side == 0 ? T.ol_hi : T.or_hi;
-            DevBuf& lo = side == 0 ? T.ol_lo : T.or_lo;
-            const auto& off = side == 0 ? offL : offR;
-            for (size_t i = 0; i < O.cls[c0].blocks.size(); ++i) {
-                const OpBlock& bb = O.cls[c0].blocks[i];
-                const long long per = (long long)bb.rows * pad8(bb.cols);
-                for (int k = 0; k < 2; ++k) {
-                    GBD_CHECK_CUDA(cudaMemsetAsync(hi.as<__nv_bfloat16>() + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
-                    GBD_CHECK_CUDA(cudaMemsetAsync(lo.as<__nv_bfloat16>() + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+    if (!T.blk) return;
+    int c0 = H.OL.state_class[sI];
+    GBD_REQUIRE(c0 == H.OL.state_class[sF], GBD_ERR_STATE, "block terms in different classes");
+    const int lay[2] = {H.OL.state_layer[sI], H.OL.state_layer[sF]};
+    std::vector<long long> xoff(H.sq.size() * 2);
+    long long xt = 0;
+    for (size_t q = 0; q < H.sq.size(); ++q)
+        for (int k = 0; k < 2; ++k) {
+            xoff[q * 2 + k] = xt;
+            xt += (long long)H.bL.dim[H.sL[q]] * H.bR.dim[H.sR[q]];
+        }
+    T.blk_x.ensure(size_t(std::max(xt, 1LL)) * 8);
+    T.blk_a.clear();
+    T.blk_b.clear();
+    for (int side = 0; side < 2; ++side) {
+        const OpSet& O = side == 0 ? H.OL : H.OR;
+        __nv_bfloat16* base = side == 0 ? P.ol.as<__nv_bfloat16>() : P.orr.as<__nv_bfloat16>();
+        const long long plane = side == 0 ? P.nL : P.nR;
+        const auto& off = side == 0 ? offL : offR;
+        for (size_t i = 0; i < O.cls[c0].blocks.size(); ++i) {
+            const OpBlock& bb = O.cls[c0].blocks[i];
+            const long long per = (long long)bb.rows * pad8(bb.cols);
+            for (int k = 0; k < 2; ++k)
+                for (int q = 0; q < 2; ++q)
+                    GBD_CHECK_CUDA(cudaMemsetAsync(base + q * plane + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+        }
+    }
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        int bl = -1, br = -1;
+        for (size_t x = 0; x < H.OL.cls[c0].blocks.size(); ++x)
+            if (H.OL.cls[c0].blocks[x].Qo == H.sq[q] && H.OL.cls[c0].blocks[x].Qi == H.sq[q]) bl = int(x);
+        for (size_t x = 0; x < H.OR.cls[c0].blocks.size(); ++x)
+            if (H.OR.cls[c0].blocks[x].Qo == H.sq[q] && H.OR.cls[c0].blocks[x].Qi == H.sq[q]) br = int(x);
+        if (bl < 0 || br < 0) continue;
+        const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
+        std::vector<GemmSeg> segB;
+        for (int k = 0; k < 2; ++k) {
+            GemmTask ta{};
+            ta.C = T.blk_x.as<double>() + xoff[q * 2 + k];
+            ta.ldc = mR; ta.M = mL; ta.N = mR; ta.nbatch = 1;
+            GemmSeg ga{};
+            ga.A = H.OL.data.as<double>() + H.OL.cls[c0].blocks[bl].off + (long long)lay[k] * mL * mL;
+            ga.lda = mL;
+            ga.B = H.xin.as<double>() + H.soff[q];
+            ga.ldb = mR; ga.K = mL; ga.T = 1; ga.coef = 1.0;
+            T.blk_a.add_task(ta, {ga});
+            GemmSeg gb{};
+            gb.A = T.blk_x.as<double>() + xoff[q * 2 + k];
+            gb.lda = mR;
+            gb.B = H.OR.data.as<double>() + H.OR.cls[c0].blocks[br].off + (long long)lay[k] * mR * mR;
+            gb.ldb = mR; gb.transB = 1; gb.K = mR; gb.T = 1; gb.coef = 1.0;
+            segB.push_back(gb);
+        }
+        GemmTask tb{};
+        tb.C = H.yout.as<double>() + H.soff[q];
+        tb.ldc = mR; tb.M = mL; tb.N = mR; tb.nbatch = 1; tb.beta = 1.0;
+        T.blk_b.add_task(tb, segB);
+    }
+    std::vector<std::pair<const void*, size_t>> bufs = {{H.OL.data.p, size_t(H.OL.total) * 8},
+                                                        {H.OR.data.p, size_t(H.OR.total) * 8},
+                                                        {T.blk_x.p, T.blk_x.bytes}, {H.xin.p, H.xin.bytes},
+                                                        {H.yout.p, H.yout.bytes}};
+    T.blk_a.check(bufs, "mixed/block-a");
+    T.blk_b.check(bufs, "mixed/block-b");
+    T.blk_a.upload(st);
+    T.blk_b.upload(st);
+}
+
+// Slice planes, tensor maps and work lists of one product form.
+template <int MODE> void build_plan(Ctx& C) {
+    using K_ = KT<MODE>;
+    constexpr int NS = K_::NS, TBN = K_::BN;
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    TcPlan& P = T.pl[MODE];
+    cudaStream_t st = C.cs;
+    const double t0 = wall_ms();
+    // ---- operator slice planes
+    std::vector<std::vector<long long>> offL, offR;
+    P.nL = std::max(op_layout(H.OL, offL), 8LL);
+    P.nR = std::max(op_layout(H.OR, offR), 8LL);
+    P.ol.ensure(size_t(P.nL) * NS * 2);
+    P.orr.ensure(size_t(P.nR) * NS * 2);
+    P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
+    {
+        DevBuf d;
+        std::vector<SplitDesc> sd;
+        auto add = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& dst, long long plane) {
+            for (size_t c = 0; c < O.cls.size(); ++c)
+                for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
+                    const OpBlock& b = O.cls[c].blocks[i];
+                    const long long rows = (long long)O.cls[c].states.size() * b.rows;
+                    const int ldd = pad8(b.cols);
+                    const long long per = std::max<long long>(1, kSplitUnits / ((ldd + 63) / 64));
+                    for (long long r0 = 0; r0 < rows; r0 += per)
+                        sd.push_back({O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
+                                      b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i] + r0 * ldd, plane});
                 }
+        };
+        add(H.OL, offL, P.ol, P.nL);
+        add(H.OR, offR, P.orr, P.nR);
+        if (!sd.empty()) {
+            upload_vec(d, sd, st);
+            for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
+                const unsigned n = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
+                split_kernel<MODE><<<n, 256, 0, st>>>(d.as<SplitDesc>() + i0);
+                count_launch();
             }
+            GBD_CHECK_CUDA(cudaGetLastError());
+            GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffer is freed on return
         }
-        for (size_t q = 0; q < H.sq.size(); ++q) {
-            int bl = -1, br = -1;
-            for (size_t x = 0; x < H.OL.cls[c0].blocks.size(); ++x)
-                if (H.OL.cls[c0].blocks[x].Qo == H.sq[q] && H.OL.cls[c0].blocks[x].Qi == H.sq[q]) bl = int(x);
-            for (size_t x = 0; x < H.OR.cls[c0].blocks.size(); ++x)
-                if (H.OR.cls[c0].blocks[x].Qo == H.sq[q] && H.OR.cls[c0].blocks[x].Qi == H.sq[q]) br = int(x);
-            if (bl < 0 || br < 0) continue;
-            const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
-            std::vector<GemmSeg> segB;
-            for (int k = 0; k < 2; ++k) {
-                GemmTask ta{};
-                ta.C = T.blk_x.as<double>() + xoff[q * 2 + k];
-                ta.ldc = mR; ta.M = mL; ta.N = mR; ta.nbatch = 1;
-                GemmSeg ga{};
-                ga.A = H.OL.data.as<double>() + H.OL.cls[c0].blocks[bl].off + (long long)lay[k] * mL * mL;
-                ga.lda = mL;
-                ga.B = H.xin.as<double>() + H.soff[q];
-                ga.ldb = mR; ga.K = mL; ga.T = 1; ga.coef = 1.0;
-                T.blk_a.add_task(ta, {ga});
-                GemmSeg gb{};
-                gb.A = T.blk_x.as<double>() + xoff[q * 2 + k];
-                gb.lda = mR;
-                gb.B = H.OR.data.as<double>() + H.OR.cls[c0].blocks[br].off + (long long)lay[k] * mR * mR;
-                gb.ldb = mR; gb.transB = 1; gb.K = mR; gb.T = 1; gb.coef = 1.0;
-                segB.push_back(gb);
-            }
-            GemmTask tb{};
-            tb.C = H.yout.as<double>() + H.soff[q];
-            tb.ldc = mR; tb.M = mL; tb.N = mR; tb.nbatch = 1; tb.beta = 1.0;
-            T.blk_b.add_task(tb, segB);
+    }
+    const double t1 = wall_ms();
+    if (MODE == 0) build_block_terms(C, P, offL, offR);
+    // ---- psi^T slice planes
+    P.np = 8;
+    for (const auto& ps : T.psec) P.np = std::max(P.np, ps.dst + (long long)ps.mR * ps.ldp);
+    P.psi.ensure(size_t(P.np) * NS * 2);
+    {
+        // psi^T per sector: row n of the operand is column n of psi
+        std::vector<SplitDesc> sd;
+        for (const auto& ps : T.psec) {
+            // psi is small and read transposed: many short descriptors keep enough loads in flight
+            const long long per = std::max<long long>(1, 32 / ((ps.ldp + 63) / 64));
+            for (long long r0 = 0; r0 < ps.mR; r0 += per)
+                sd.push_back({H.xin.as<double>() + ps.src + r0, 1, ps.mR, std::min<long long>(per, ps.mR - r0), ps.mL,
+                              ps.ldp, P.psi.as<__nv_bfloat16>() + ps.dst + r0 * ps.ldp, P.np});
         }
-        std::vector<std::pair<const void*, size_t>> bufs = {{H.OL.data.p, size_t(H.OL.total) * 8},
-                                                            {H.OR.data.p, size_t(H.OR.total) * 8},
-                                                            {T.blk_x.p, T.blk_x.bytes}, {H.xin.p, H.xin.bytes},
-                                                            {H.yout.p, H.yout.bytes}};
-        T.blk_a.check(bufs, "mixed/block-a");
-        T.blk_b.check(bufs, "mixed/block-b");
-        T.blk_a.upload(st);
-        T.blk_b.upload(st);
+        upload_vec(P.psi_split, sd, st);
+        P.n_psi = int(sd.size());
     }
-    // ---- psi^T sectors
-    long long np = 0;
-    for (size_t s = 0; s < H.sq.size(); ++s) {
-        int mL = H.bL.dim[H.sL[s]], mR = H.bR.dim[H.sR[s]];
-        T.psec.push_back({H.soff[s], np, mL, mR, pad8(mL)});
-        np += (long long)mR * pad8(mL);
-    }
-    T.psi_hi.ensure(size_t(std::max(np, 8LL)) * 2);
-    T.psi_lo.ensure(size_t(std::max(np, 8LL)) * 2);
-    T.psec_dev.ensure(T.psec.size() * sizeof(TcHeff::PsiSec));
-    GBD_CHECK_CUDA(cudaMemcpyAsync(T.psec_dev.p, T.psec.data(), T.psec.size() * sizeof(TcHeff::PsiSec),
-                                   cudaMemcpyHostToDevice, st));
     // ---- pairs (class, block) with their phase-1 outputs X
     struct Pair { int c, bl, br, so, si; long long x; };
     std::vector<Pair> pairs;
@@ -639,22 +854,20 @@ void tc_prepare(Ctx& C) {
             nx += (long long)cl.states.size() * H.bL.dim[H.sL[so]] * pad8(H.bR.dim[H.sR[si]]);
         }
     }
-    T.x_hi.ensure(size_t(std::max(nx, 8LL)) * 2);
-    T.x_lo.ensure(size_t(std::max(nx, 8LL)) * 2);
-    // ---- tensor maps
+    P.nx = std::max(nx, 8LL);
+    P.x.ensure(size_t(P.nx) * NS * 2);
+    // ---- tensor maps: one per operand, the NS slice planes as outer dimension
     std::vector<CUtensorMap> maps;
-    auto add_pair_maps = [&](const void* hi, const void* lo, int K, long long rows, int layers, int ld, long long lp,
-                             int box_rows) {
+    auto add_maps = [&](const __nv_bfloat16* base, long long plane, int K, long long rows, int layers, int ld,
+                        long long lp, int box_rows) {
         int id = int(maps.size());
-        maps.push_back(make_map(hi, K, rows, layers, ld, lp, box_rows));
-        maps.push_back(make_map(lo, K, rows, layers, ld, lp, box_rows));
+        maps.push_back(make_map(base, K, rows, layers, ld, lp, NS, plane, box_rows));
         return id;
     };
     std::vector<int> psi_map(H.sq.size());
     for (size_t s = 0; s < H.sq.size(); ++s) {
         const auto& ps = T.psec[s];
-        psi_map[s] = add_pair_maps(T.psi_hi.as<__nv_bfloat16>() + ps.dst, T.psi_lo.as<__nv_bfloat16>() + ps.dst, ps.mL,
-                                   ps.mR, 0, ps.ldp, 0, BN);
+        psi_map[s] = add_maps(P.psi.as<__nv_bfloat16>() + ps.dst, P.np, ps.mL, ps.mR, 0, ps.ldp, 0, TBN);
     }
     std::vector<KSeg> s1, s2;
     std::vector<Work> w1, w2;
@@ -667,12 +880,11 @@ void tc_prepare(Ctx& C) {
         const int mRo = H.bR.dim[H.sR[p.so]], mRi = H.bR.dim[H.sR[p.si]];
         // phase 1: X (Tn*mLo x mRi) = OL_stacked (Tn*mLo x mLi) psi (mLi x mRi), psi^T K-major
         const long long ol = offL[p.c][p.bl];
-        int mA = add_pair_maps(T.ol_hi.as<__nv_bfloat16>() + ol, T.ol_lo.as<__nv_bfloat16>() + ol, mLi,
-                               (long long)Tn * mLo, 0, pad8(mLi), 0, BM);
+        int mA = add_maps(P.ol.as<__nv_bfloat16>() + ol, P.nL, mLi, (long long)Tn * mLo, 0, pad8(mLi), 0, BM);
         int sidx = int(s1.size());
         s1.push_back({mA, psi_map[p.si], 0, 0, mLi, 1, 2, (mLi + BK - 1) / BK});
         for (long long m0 = 0; m0 < (long long)Tn * mLo; m0 += BM)
-            for (int n0 = 0; n0 < mRi; n0 += BN) {
+            for (int n0 = 0; n0 < mRi; n0 += TBN) {
                 Work w{};
                 w.m0 = int(m0);
                 w.n0 = n0;
@@ -683,18 +895,16 @@ void tc_prepare(Ctx& C) {
                 w.c0 = 0;
                 w.c1 = s1[sidx].nchunk;
                 w.out_kind = 1;
-                w.promote = 1 << 30;
+                w.promote = MODE == 0 ? (1 << 30) : 1;
                 w.ldo = pad8(mRi);
-                w.out_hi = T.x_hi.as<__nv_bfloat16>() + p.x;
-                w.out_lo = T.x_lo.as<__nv_bfloat16>() + p.x;
+                w.plane = P.nx;
+                w.out = P.x.as<__nv_bfloat16>() + p.x;
                 w1.push_back(w);
             }
         // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn
-        int mX = add_pair_maps(T.x_hi.as<__nv_bfloat16>() + p.x, T.x_lo.as<__nv_bfloat16>() + p.x, mRi, mLo, Tn,
-                               pad8(mRi), (long long)mLo * pad8(mRi), BM);
+        int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
         const long long orr = offR[p.c][p.br];
-        int mO = add_pair_maps(T.or_hi.as<__nv_bfloat16>() + orr, T.or_lo.as<__nv_bfloat16>() + orr, mRi, mRo, Tn,
-                               pad8(mRi), (long long)mRo * pad8(mRi), BN);
+        int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi), TBN);
         seg_of_out[p.so].push_back(int(s2.size()));
         s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
     }
@@ -703,10 +913,10 @@ void tc_prepare(Ctx& C) {
     for (size_t q = 0; q < H.sq.size(); ++q) {
         long long c = 0;
         for (int si : seg_of_out[q]) c += s2[si].nchunk;
-        int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + BN - 1) / BN);
+        int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + TBN - 1) / TBN);
         total_chunks += c * tiles;
     }
-    const long long target = std::max<long long>(16, total_chunks / (4 * 152) + 1);
+    const long long target = std::max<long long>(16, total_chunks / (4 * T.n_sm) + 1);
     std::vector<KSeg> s2o;  // segments re-laid per output sector (contiguous)
     long long npart = 0;
     for (size_t q = 0; q < H.sq.size(); ++q) {
@@ -716,7 +926,7 @@ void tc_prepare(Ctx& C) {
         int nseg = int(s2o.size()) - seg0;
         const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
         for (int m0 = 0; m0 < mL; m0 += BM)
-            for (int n0 = 0; n0 < mR; n0 += BN) {
+            for (int n0 = 0; n0 < mR; n0 += TBN) {
                 Reduce r{};
                 r.out = H.yout.as<double>() + H.soff[q];
                 r.ldo = mR;
@@ -724,6 +934,7 @@ void tc_prepare(Ctx& C) {
                 r.n0 = n0;
                 r.M = mL;
                 r.N = mR;
+                r.bn = TBN;
                 r.p0 = int(npart);
                 for (int c0 = 0; c0 < nchunk; c0 += int(target)) {
                     Work w{};
@@ -736,9 +947,9 @@ void tc_prepare(Ctx& C) {
                     w.c0 = c0;
                     w.c1 = int(std::min<long long>(nchunk, c0 + target));
                     w.out_kind = 0;
-                    w.promote = 8;
-                    w.ldo = BN;
-                    w.out_hi = reinterpret_cast<void*>(npart);  // patched to a pointer below
+                    w.promote = MODE == 0 ? 8 : 1;
+                    w.ldo = TBN;
+                    w.out = reinterpret_cast<void*>(npart);  // patched to a pointer below
                     w2.push_back(w);
                     ++npart;
                 }
@@ -746,79 +957,117 @@ void tc_prepare(Ctx& C) {
                 red.push_back(r);
             }
     }
-    T.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * BN * sizeof(float2));
-    for (auto& w : w2) w.out_hi = T.partial.as<float2>() + reinterpret_cast<long long>(w.out_hi) * BM * BN;
-    // tensor-core work issued per product (three split MMAs per K step,
-    // whole 128 x 128 x 64 tiles): the gap to the useful flops is padding
+    P.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2));
+    for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
+    // tensor-core work issued per product (whole tiles, every slice product):
+    // the gap to the useful flops is padding
     auto issued = [](const std::vector<Work>& ws) {
         double f = 0.0;
-        for (const auto& w : ws) f += double(w.c1 - w.c0) * BM * BN * BK * 2.0 * 3.0;
+        for (const auto& w : ws) f += double(w.c1 - w.c0) * BM * TBN * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
         return f * 1e-9;
     };
-    C.timers[Ctx::T_TC_ISSUE1] = issued(w1);
-    C.timers[Ctx::T_TC_ISSUE2] = issued(w2);
+    P.issued_p1 = issued(w1);
+    P.issued_p2 = issued(w2);
     // persistent CTAs take items round-robin: longest first evens out the tail
     auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
     std::stable_sort(w1.begin(), w1.end(), longer);
     std::stable_sort(w2.begin(), w2.end(), longer);
+    const double t2 = wall_ms();
     // ---- upload
-    T.maps.ensure(std::max<size_t>(maps.size(), 1) * sizeof(CUtensorMap));
-    GBD_CHECK_CUDA(cudaMemcpyAsync(T.maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
-    auto up = [&](DevBuf& d, const void* src, size_t bytes) {
-        d.ensure(std::max<size_t>(bytes, 16));
-        if (bytes) GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, st));
-    };
-    up(T.w1, w1.data(), w1.size() * sizeof(Work));
-    up(T.s1, s1.data(), s1.size() * sizeof(KSeg));
-    up(T.w2, w2.data(), w2.size() * sizeof(Work));
-    up(T.s2, s2o.data(), s2o.size() * sizeof(KSeg));
-    up(T.red, red.data(), red.size() * sizeof(Reduce));
-    T.err.ensure(sizeof(int));
-    GBD_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
-    T.n_w1 = int(w1.size());
-    T.n_w2 = int(w2.size());
-    T.n_red = int(red.size());
-    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    {
+    upload_vec(P.maps, maps, st);
+    upload_vec(P.w1, w1, st);
+    upload_vec(P.s1, s1, st);
+    upload_vec(P.w2, w2, st);
+    upload_vec(P.s2, s2o, st);
+    upload_vec(P.red, red, st);
+    P.n_w1 = int(w1.size());
+    P.n_w2 = int(w2.size());
+    P.n_red = int(red.size());
+    GBD_CHECK_CUDA(
+        cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, K_::SMEM_BYTES));
+    GBD_CHECK_CUDA(cudaStreamSynchronize(st));
+    P.built = true;
+    C.timers[Ctx::T_PREP_SPLIT] += t1 - t0;
+    C.timers[Ctx::T_PREP_PLAN] += t2 - t1;
+    C.timers[Ctx::T_PREP_UPLOAD] += wall_ms() - t2;
+}
+
+}  // namespace
+
+// Builds the slice planes, tensor maps and work lists of one product form
+// (0: BF16x3, 1: sliced) for the current position.
+void tc_prepare(Ctx& C, int mode) {
+    GBD_REQUIRE(mode == 0 || mode == 1, GBD_ERR_ARG, "tensor-core product form must be 0 or 1");
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    cudaStream_t st = C.cs;
+    if (!H.tc_ready) {
+        // shared by both forms: psi^T sector layout, error word, SM count
+        T.psec.clear();
+        long long np = 0;
+        for (size_t s = 0; s < H.sq.size(); ++s) {
+            int mL = H.bL.dim[H.sL[s]], mR = H.bR.dim[H.sR[s]];
+            T.psec.push_back({H.soff[s], np, mL, mR, pad8(mL)});
+            np += (long long)mR * pad8(mL);
+        }
+        T.err.ensure(sizeof(int));
+        GBD_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
         int dev = 0;
         GBD_CHECK_CUDA(cudaGetDevice(&dev));
         GBD_CHECK_CUDA(cudaDeviceGetAttribute(&T.n_sm, cudaDevAttrMultiProcessorCount, dev));
         T.n_sm = std::max(T.n_sm, 1);
+        T.pl[0].built = T.pl[1].built = false;
+        H.tc_ready = true;
     }
-    GBD_CHECK_CUDA(cudaStreamSynchronize(st));
-    T.built = true;
-    H.tc_ready = true;
+    if (!T.pl[mode].built) {
+        if (mode == 0) {
+            build_plan<0>(C);
+            C.timers[Ctx::T_TC_ISSUE1] = T.pl[0].issued_p1;
+            C.timers[Ctx::T_TC_ISSUE2] = T.pl[0].issued_p2;
+        } else {
+            build_plan<1>(C);
+            C.timers[Ctx::T_TC_ISSUE_SL] = T.pl[1].issued_p1 + T.pl[1].issued_p2;
+        }
+    }
 }
 
-// One mixed-precision product: H.xin (FP64) -> H.yout (FP64).
-void tc_apply(Ctx& C) {
+namespace {
+template <int MODE> void run_plan(Ctx& C) {
+    using K_ = KT<MODE>;
     Heff& H = C.H;
     TcHeff& T = H.tc;
+    TcPlan& P = T.pl[MODE];
     cudaStream_t st = C.cs;
-    if (!T.psec.empty()) {
-        split_psi_kernel<<<dim3(16, unsigned(T.psec.size())), 256, 0, st>>>(
-            H.xin.as<double>(), T.psec_dev.as<TcHeff::PsiSec>(), T.psi_hi.as<__nv_bfloat16>(), T.psi_lo.as<__nv_bfloat16>());
+    if (P.n_psi > 0) {
+        split_kernel<MODE><<<unsigned(P.n_psi), 256, 0, st>>>(P.psi_split.as<SplitDesc>());
         count_launch();
     }
-    if (T.n_w1 > 0) {
-        tc_gemm_kernel<<<std::min(T.n_w1, T.n_sm), THREADS, SMEM_BYTES, st>>>(
-            T.w1.as<Work>(), T.n_w1, T.s1.as<KSeg>(), T.maps.as<CUtensorMap>(), T.err.as<int>());
+    if (P.n_w1 > 0) {
+        tc_gemm_kernel<MODE><<<std::min(P.n_w1, T.n_sm), THREADS, K_::SMEM_BYTES, st>>>(
+            P.w1.as<Work>(), P.n_w1, P.s1.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
         count_launch();
     }
-    if (T.n_red > 0) {
-        if (T.n_w2 > 0) {
-            tc_gemm_kernel<<<std::min(T.n_w2, T.n_sm), THREADS, SMEM_BYTES, st>>>(
-                T.w2.as<Work>(), T.n_w2, T.s2.as<KSeg>(), T.maps.as<CUtensorMap>(), T.err.as<int>());
+    if (P.n_red > 0) {
+        if (P.n_w2 > 0) {
+            tc_gemm_kernel<MODE><<<std::min(P.n_w2, T.n_sm), THREADS, K_::SMEM_BYTES, st>>>(
+                P.w2.as<Work>(), P.n_w2, P.s2.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
             count_launch();
         }
-        reduce_kernel<<<T.n_red, 256, 0, st>>>(T.red.as<Reduce>(), T.partial.as<float2>());
+        reduce_kernel<<<P.n_red, 256, 0, st>>>(P.red.as<Reduce>(), P.partial.as<float2>());
         count_launch();
     }
-    if (T.blk) {
+    if (MODE == 0 && T.blk) {
         T.blk_a.launch(st);
         T.blk_b.launch(st);
     }
     GBD_CHECK_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+// One tensor-core product: H.xin (FP64) -> H.yout (FP64).
+void tc_apply(Ctx& C, int mode) {
+    GBD_REQUIRE(C.H.tc_ready && C.H.tc.pl[mode].built, GBD_ERR_STATE, "tensor-core plan not prepared");
+    if (mode == 0) run_plan<0>(C); else run_plan<1>(C);
 }
 
 int tc_error(Ctx& C) {

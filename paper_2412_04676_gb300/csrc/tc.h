@@ -1,5 +1,16 @@
-// tc.h -- mixed-precision (BF16x3 split, FP32 accumulate, FP64 promotion)
-// H_eff products on the fifth-generation tensor cores (tcgen05 + TMEM, TMA).
+// tc.h -- H_eff products on the fifth-generation tensor cores (tcgen05 +
+// TMEM, TMA) in two forms:
+//   mode 0 (BF16x3): x = hi + lo elementwise, products hh + hl + lh, FP32
+//                    accumulation, ~1e-5 relative accuracy; the cheap product
+//                    of the mixed-precision Davidson iterations.
+//   mode 1 (sliced): error-free splitting of every operand row, per 64-wide K
+//                    block, into four BF16 slices on a common power-of-two
+//                    grid (the splitting of Ozaki et al., as used for tensor
+//                    cores by Mukunoki et al.); the ten slice products of
+//                    orders <= 4 go to three TMEM accumulators, the two
+//                    leading orders of which add up exactly in FP32.  About
+//                    2^-30 relative to the row maxima: the anchor products of
+//                    the mixed-precision Davidson.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,35 +28,37 @@ struct Ctx;
 namespace tc {
 
 constexpr int BM = 128;       // tile rows (UMMA M)
-constexpr int BN = 128;       // tile cols (UMMA N)
 constexpr int BK = 64;        // K elements per pipeline stage (one 128-byte swizzle row)
 constexpr int STAGES = 2;
 constexpr int EPI_WARPS = 16;                // four per TMEM lane quadrant
 constexpr int EPI_THREADS = EPI_WARPS * 32;
-constexpr int CP = BN / (EPI_WARPS / 4);     // accumulator columns per epilogue thread
 constexpr int THREADS = 64 + EPI_THREADS;    // warp 0 TMA, warp 1 MMA, then the epilogue warps
-constexpr int TMEM_COLS = 2 * BN;
+
+// per-mode tile shape: slices per operand, tile columns, TMEM columns per buffer
+template <int MODE> struct ModeCfg;
+template <> struct ModeCfg<0> { static constexpr int NS = 2, BN = 128, BUFCOLS = 128, TMEM_COLS = 256; };
+template <> struct ModeCfg<1> { static constexpr int NS = 4, BN = 64, BUFCOLS = 256, TMEM_COLS = 512; };
 
 // One K segment: chunks over layers t < T and inner offsets j0 < K step BK.
 struct KSeg {
-    int mapA, mapB;   // tensor-map index of the hi operand; lo is index + 1
+    int mapA, mapB;   // tensor-map index of each operand (slice planes are its outer dimension)
     int a_row, b_row; // row coordinate of the tile origin's operand rows
     int K, T;
-    int rank;         // 2 (no layer dimension) or 3
+    int rank;         // 2 (no layer dimension) or 3, not counting the slice-plane dimension
     int nchunk;       // T * ceil(K / BK)
 };
 
-// One CTA's work: an output tile and a contiguous range of K chunks.
+// One work item: an output tile and a contiguous range of K chunks.
 struct Work {
     int m0, n0;
     int M, N;          // valid rows / cols of the whole output (bounds)
     int seg0, nseg;
     int c0, c1;        // chunk range over the concatenated segments
-    int out_kind;      // 0: FP64 partial tile, 1: BF16 hi/lo matrix, 2: FP64 matrix
-    int promote;       // chunks between FP32 -> FP64 promotions
+    int out_kind;      // 0: FP32-pair partial tile, 1: BF16 slice planes, 2: FP64 matrix
+    int promote;       // chunks between promotions of the TMEM accumulators
     long long ldo;
-    void* out_hi;
-    void* out_lo;
+    long long plane;   // element distance between BF16 slice planes (kind 1)
+    void* out;
 };
 
 // Sum of split-K partial tiles into one FP64 output tile.
@@ -54,31 +67,38 @@ struct Reduce {
     long long ldo;
     int m0, n0, M, N;
     int p0, p1;        // partial tiles [p0, p1)
+    int bn;            // tile columns
 };
 
 }  // namespace tc
 
-struct TcHeff {
+// Device data of one product form: slice planes, tensor maps, work lists.
+struct TcPlan {
     bool built = false;
-    DevBuf ol_hi, ol_lo, or_hi, or_lo;      // BF16 operator arenas (rows padded to 8 elements)
-    DevBuf psi_hi, psi_lo;                  // BF16 psi^T per sector
-    DevBuf x_hi, x_lo;                      // BF16 phase-1 output
-    DevBuf maps;                            // CUtensorMap array (64-byte aligned entries)
-    DevBuf w1, s1, w2, s2, red, partial;    // work lists, segments, reductions, split-K partials
-    DevBuf err;                             // device error word
-    int n_w1 = 0, n_w2 = 0, n_red = 0, n_sm = 152;
+    long long nL = 0, nR = 0, np = 0, nx = 0;  // plane strides (elements) of the operator / psi / X slices
+    DevBuf ol, orr, psi, x;                     // BF16 slice planes
+    DevBuf maps;                                // CUtensorMap array (64-byte aligned entries)
+    DevBuf w1, s1, w2, s2, red, partial;        // work lists, segments, reductions, split-K partials
+    DevBuf psi_split;                           // splitting descriptors of psi^T (one per sector)
+    int n_w1 = 0, n_w2 = 0, n_red = 0, n_psi = 0;
+    double bytes_ops = 0.0;                     // operator slice bytes
+    double issued_p1 = 0.0, issued_p2 = 0.0;    // tensor-core GFLOP issued per product
+};
+
+struct TcHeff {
+    TcPlan pl[2];
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
     std::vector<PsiSec> psec;
-    DevBuf psec_dev;
-    double bytes_ops = 0.0;                 // BF16 operator bytes (hi + lo)
-    GemmPlan blk_a, blk_b;                  // FP64 block-Hamiltonian terms (optional)
+    DevBuf err;                             // device error word
+    int n_sm = 152;
+    GemmPlan blk_a, blk_b;                  // FP64 block-Hamiltonian terms (mode 0, optional)
     DevBuf blk_x;
     bool blk = false;
 };
 
-void tc_prepare(Ctx& C);
-void tc_apply(Ctx& C);
+void tc_prepare(Ctx& C, int mode);
+void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
 
 }  // namespace gbd
