@@ -702,10 +702,10 @@ void setup_heff(Ctx& C, int b) {
     H.yout.ensure(size_t(H.dim) * sizeof(double));
     H.diag.ensure(size_t(H.dim) * sizeof(double));
     // phase 1: X_{c,Q2}[t] = OL[t][Q,Q2] psi[Q2]; phase 2: Y[Q] += sum X[t] OR[t][Q,Q2]^T
-    struct Pair { int c, bl, br, s_out, s_in; long long xoff; };
-    std::vector<Pair> pairs;
     long long xtot = 0;
     H.op_bytes = double(H.OL.total + H.OR.total) * 8.0;
+    H.flops = 0.0;
+    double nx = 0.0;
     for (size_t c = 0; c < H.OL.cls.size(); ++c) {
         const OpClass& cl = H.OL.cls[c];
         const OpClass& cr = H.OR.cls[c];
@@ -719,11 +719,35 @@ void setup_heff(Ctx& C, int b) {
             for (size_t x = 0; x < cr.blocks.size(); ++x)
                 if (cr.blocks[x].Qo == ob.Qo && cr.blocks[x].Qi == ob.Qi) br = int(x);
             if (br < 0) continue;
-            pairs.push_back({int(c), int(bi), br, so, si, xtot});
+            H.pairs.push_back({int(c), int(bi), br, so, si, xtot});
+            const double mLo = H.bL.dim[H.sL[so]], mLi = H.bL.dim[H.sL[si]];
+            const double mRo = H.bR.dim[H.sR[so]], mRi = H.bR.dim[H.sR[si]];
             xtot += (long long)T * H.bL.dim[H.sL[so]] * H.bR.dim[H.sR[si]];
+            nx += double(T) * mLo * mRi;
+            // useful flops: 2 M N K of both phases
+            H.flops += 2.0 * T * mLo * mRi * mLi + 2.0 * mLo * mRo * (T * mRi);
+            H.ngemm += 2LL * T;
         }
     }
-    H.X.ensure(size_t(std::max<long long>(xtot, 1)) * sizeof(double));
+    H.xtot = xtot;
+    {
+        double elems = 0.0;
+        for (const OpSet* O : {&H.OL, &H.OR})
+            for (const auto& c : O->cls)
+                for (const auto& bb : c.blocks) elems += double(c.states.size()) * bb.rows * bb.cols;
+        H.mixed_bytes = 4.0 * elems + 8.0 * nx + 16.0 * double(H.dim);
+    }
+    H.fp64_ready = false;
+    H.diag_ready = false;
+    H.tc_ready = false;
+    GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+}
+
+// FP64 GEMM plans of the two phases, built at the first FP64 product of a
+// position (mixed-precision runs may never need them).
+void build_fp64_plans(Ctx& C) {
+    Heff& H = C.H;
+    H.X.ensure(size_t(std::max<long long>(H.xtot, 1)) * sizeof(double));
     const double* dOL = H.OL.data.as<double>();
     const double* dOR = H.OR.data.as<double>();
     double* dX = H.X.as<double>();
@@ -732,7 +756,7 @@ void setup_heff(Ctx& C, int b) {
     H.p1.clear();
     H.p2.clear();
     std::vector<std::vector<GemmSeg>> by_out(H.sq.size());
-    for (const auto& p : pairs) {
+    for (const auto& p : H.pairs) {
         const OpClass& cl = H.OL.cls[p.c];
         const OpBlock& ob = cl.blocks[p.bl];
         const OpBlock& rb = H.OR.cls[p.c].blocks[p.br];
@@ -766,7 +790,6 @@ void setup_heff(Ctx& C, int b) {
         g2.T = T;
         g2.coef = 1.0;
         by_out[p.s_out].push_back(g2);
-        H.ngemm += 2LL * T;
     }
     for (size_t s = 0; s < H.sq.size(); ++s) {
         GemmTask t2{};
@@ -778,17 +801,6 @@ void setup_heff(Ctx& C, int b) {
         t2.beta = 0.0;
         H.p2.add_task(t2, by_out[s]);
     }
-    H.flops = H.p1.flops + H.p2.flops;
-    {
-        double elems = 0.0;
-        for (const OpSet* O : {&H.OL, &H.OR})
-            for (const auto& c : O->cls)
-                for (const auto& bb : c.blocks) elems += double(c.states.size()) * bb.rows * bb.cols;
-        double nx = 0.0;
-        for (const auto& p : pairs)
-            nx += double(H.OL.cls[p.c].states.size()) * H.bL.dim[H.sL[p.s_out]] * H.bR.dim[H.sR[p.s_in]];
-        H.mixed_bytes = 4.0 * elems + 8.0 * nx + 16.0 * double(H.dim);
-    }
     std::vector<std::pair<const void*, size_t>> bufs = {{H.OL.data.p, size_t(H.OL.total) * 8},
                                                         {H.OR.data.p, size_t(H.OR.total) * 8},
                                                         {H.X.p, H.X.bytes}, {H.xin.p, H.xin.bytes},
@@ -797,9 +809,8 @@ void setup_heff(Ctx& C, int b) {
     H.p2.check(bufs, "heff/phase2");
     H.p1.upload(C.cs);
     H.p2.upload(C.cs);
-    H.diag_ready = false;
-    H.tc_ready = false;
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+    H.fp64_ready = true;
 }
 
 
@@ -818,6 +829,10 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
         }
         tc_apply(C, mode);
     } else {
+        if (!H.fp64_ready) {
+            build_fp64_plans(C);
+            GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
+        }
         H.p1.launch(C.cs);
         H.p2.launch(C.cs);
     }

@@ -54,7 +54,11 @@ struct Heff {
     std::vector<long long> soff;
     long long dim = 0;
     OpSet OL, OR;
-    GemmPlan p1, p2;
+    GemmPlan p1, p2;         // FP64 product plans (built at the first FP64 product)
+    bool fp64_ready = false;
+    struct Pair { int c, bl, br, s_out, s_in; long long xoff; };
+    std::vector<Pair> pairs; // (class, left block, right block) with matching sectors
+    long long xtot = 0;      // FP64 phase-1 output elements
     DevBuf X, xin, yout, diag;
     bool diag_ready = false;
     long long ngemm = 0;
