@@ -330,8 +330,9 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * products in each form, then the tensor-core GFLOP one GBD_SLICED_BF16
  * product issues (ten slice products; not accumulated), then the host wall
  * time (ms) of the tensor-core operand preparation in three parts: operator
- * splitting, planning (work lists, tensor maps), upload.  *n gets the count;
- * out may be NULL. */
+ * splitting, planning (work lists, tensor maps), upload, then the useful
+ * GFLOP of the H_eff products in each of the three forms.  *n gets the
+ * count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

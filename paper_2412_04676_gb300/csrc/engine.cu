@@ -849,6 +849,7 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     C.matvec_count += 1;
     C.timers[Ctx::T_PROD_MS0 + precision] += ms;
     C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
+    C.timers[Ctx::T_PROD_GF0 + precision] += H.flops * 1e-9;
 }
 
 void heff_diag(Ctx& C) {

@@ -41,10 +41,12 @@ template <int MODE> struct KT {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
     static constexpr int CP = BN / 4;                        // accumulator columns per epilogue thread
-    static constexpr int RS = BN * 2 + 16;                   // padded row stride of a BF16 staging tile
-    static constexpr int EPI_BYTES = (MODE == 0 ? 2 : 1) * BM * RS;  // hi + lo, or one slice at a time
+    static constexpr int ST = ModeCfg<MODE>::STAGES;
+    static constexpr int RS = BN * 2;                        // row stride of the BF16 staging tile (XOR-swizzled)
+    static constexpr int EPI_BYTES = BM * RS;                // one output plane at a time
     static constexpr int RMAX_BYTES = MODE == 1 ? 4 * BM * 4 : 0;    // row maxima of the four column parts
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + RMAX_BYTES + 1024;
+    static constexpr int SMEM_BYTES = ST * STAGE_BYTES + EPI_BYTES + RMAX_BYTES + 1024;
+    static_assert(ST <= MAX_STAGES, "barrier arrays");
     // instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN
     static constexpr uint32_t IDESC =
         (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
@@ -174,16 +176,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
     using K_ = KT<MODE>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* epi = smem + STAGES * K_::STAGE_BYTES;
+    uint8_t* epi = smem + K_::ST * K_::STAGE_BYTES;
     float* rmax = reinterpret_cast<float*>(epi + K_::EPI_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < K_::ST; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
@@ -215,8 +217,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             int s, t, j0;
             locate(segs, w.seg0, w.nseg, w.c0, s, t, j0);
             for (int i = 0; i < n; ++i, ++g) {
-                const int st = int(g % STAGES);
-                if (g >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), uint32_t(((g / STAGES) & 1) ^ 1))) {
+                const int st = int(g % K_::ST);
+                if (g >= K_::ST && !mbar_wait(smem_u32(&empty_bar[st]), uint32_t(((g / K_::ST) & 1) ^ 1))) {
                     atomicExch(err, 1);
                     abort_s = 1;
                     break;
@@ -250,8 +252,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         }
         // on abort: let the loads already issued land before the CTA may exit
         if (abort_s)
-            for (long long i = (g > STAGES ? g - STAGES : 0); i < g; ++i)
-                mbar_wait(smem_u32(&full_bar[i % STAGES]), uint32_t((i / STAGES) & 1));
+            for (long long i = (g > K_::ST ? g - K_::ST : 0); i < g; ++i)
+                mbar_wait(smem_u32(&full_bar[i % K_::ST]), uint32_t((i / K_::ST) & 1));
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         long long g = 0;   // chunks consumed
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             const int promote = w.promote > 0 ? w.promote : (1 << 30);
             int inbuf = 0;
             for (int i = 0; i < n; ++i, ++g) {
-                const int st = int(g % STAGES);
-                if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / STAGES) & 1))) {
+                const int st = int(g % K_::ST);
+                if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / K_::ST) & 1))) {
                     atomicExch(err, 2);
                     abort_s = 1;
                     break;
@@ -389,38 +391,39 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int et = threadIdx.x - 64;  // 0 .. EPI_THREADS - 1
                 constexpr int vpr = K_::BN / 8;   // 16-byte vectors per row
                 if constexpr (MODE == 0) {
-                    // BF16 hi / lo through the staging tile, then coalesced
-                    // 16-byte stores of whole rows
-                    uint8_t* sh = epi;
-                    uint8_t* sl = epi + BM * K_::RS;
-                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // previous item's readers are done
+                    // BF16 hi / lo, one plane at a time through the staging
+                    // tile (16-byte vectors XOR-swizzled by row), then
+                    // coalesced 16-byte stores of whole rows
+                    uint32_t ph[CP / 2], pl[CP / 2];
 #pragma unroll
-                    for (int i = 0; i < CP; i += 8) {
-                        uint32_t ph[4], pl[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            // x - bf16(x) is exact in FP32, so the split needs no FP64
-                            const float x0 = ah[i + 2 * k] + al[i + 2 * k], x1 = ah[i + 2 * k + 1] + al[i + 2 * k + 1];
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
-                            const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
-                            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-                            ph[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
-                            pl[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
-                        }
-                        const int cb = (part * CP + i) * 2;
-                        *reinterpret_cast<uint4*>(sh + row * K_::RS + cb) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                        *reinterpret_cast<uint4*>(sl + row * K_::RS + cb) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                    for (int i = 0; i < CP; i += 2) {
+                        // x - bf16(x) is exact in FP32, so the split needs no FP64
+                        const float x0 = ah[i] + al[i], x1 = ah[i + 1] + al[i + 1];
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                        ph[i / 2] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+                        pl[i / 2] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
                     }
-                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // all epilogue warps
-                    for (int v = et; v < BM * vpr; v += EPI_THREADS) {
-                        const int r = v / vpr, c8 = (v % vpr) * 8;
-                        const int grow = w.m0 + r, gcol = w.n0 + c8;
-                        if (grow >= w.M || gcol >= ldo) continue;
-                        const uint4 hv = *reinterpret_cast<const uint4*>(sh + r * K_::RS + c8 * 2);
-                        const uint4 lv = *reinterpret_cast<const uint4*>(sl + r * K_::RS + c8 * 2);
-                        *reinterpret_cast<uint4*>(o0 + grow * ldo + gcol) = hv;
-                        *reinterpret_cast<uint4*>(o0 + w.plane + grow * ldo + gcol) = lv;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const uint32_t* pk = q == 0 ? ph : pl;
+                        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // earlier readers are done
+#pragma unroll
+                        for (int j = 0; j < CP / 8; ++j) {
+                            const int v = part * (CP / 8) + j;
+                            *reinterpret_cast<uint4*>(epi + row * K_::RS + ((v ^ (row & (vpr - 1))) << 4)) =
+                                make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                        }
+                        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                        for (int v = et; v < BM * vpr; v += EPI_THREADS) {
+                            const int r = v / vpr, cv = v % vpr;
+                            const int grow = w.m0 + r, gcol = w.n0 + cv * 8;
+                            if (grow >= w.M || gcol >= ldo) continue;
+                            *reinterpret_cast<uint4*>(o0 + q * w.plane + grow * ldo + gcol) =
+                                *reinterpret_cast<const uint4*>(epi + r * K_::RS + ((cv ^ (r & (vpr - 1))) << 4));
+                        }
                     }
                 } else {
                     // four slices on the grid of this row's maximum over the
@@ -464,16 +467,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                     for (int q = 0; q < 4; ++q) {
                         if (q > 0) asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // plane q-1 copied out
 #pragma unroll
-                        for (int i = 0; i < CP / 2; i += 4)
-                            *reinterpret_cast<uint4*>(epi + row * K_::RS + part * CP * 2 + i * 4) =
+                        for (int i = 0; i < CP / 2; i += 4) {
+                            const int v = (part * CP * 2 + i * 4) >> 4;
+                            *reinterpret_cast<uint4*>(epi + row * K_::RS + ((v ^ (row & (vpr - 1))) << 4)) =
                                 make_uint4(pk[q][i], pk[q][i + 1], pk[q][i + 2], pk[q][i + 3]);
+                        }
                         asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
                         for (int v = et; v < BM * vpr; v += EPI_THREADS) {
                             const int r = v / vpr, c8 = (v % vpr) * 8;
                             const int grow = w.m0 + r, gcol = w.n0 + c8;
                             if (grow >= w.M || gcol >= ldo) continue;
                             *reinterpret_cast<uint4*>(o0 + q * w.plane + grow * ldo + gcol) =
-                                *reinterpret_cast<const uint4*>(epi + r * K_::RS + c8 * 2);
+                                *reinterpret_cast<const uint4*>(epi + r * K_::RS + (((c8 >> 3) ^ (r & (vpr - 1))) << 4));
                         }
                     }
                 }

@@ -29,15 +29,16 @@ namespace tc {
 
 constexpr int BM = 128;       // tile rows (UMMA M)
 constexpr int BK = 64;        // K elements per pipeline stage (one 128-byte swizzle row)
-constexpr int STAGES = 2;
+constexpr int MAX_STAGES = 3;
 constexpr int EPI_WARPS = 16;                // four per TMEM lane quadrant
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int THREADS = 64 + EPI_THREADS;    // warp 0 TMA, warp 1 MMA, then the epilogue warps
 
-// per-mode tile shape: slices per operand, tile columns, TMEM columns per buffer
+// per-mode tile shape: slices per operand, tile columns, TMEM columns per
+// buffer, pipeline stages (as many as fit in shared memory)
 template <int MODE> struct ModeCfg;
-template <> struct ModeCfg<0> { static constexpr int NS = 2, BN = 128, BUFCOLS = 128, TMEM_COLS = 256; };
-template <> struct ModeCfg<1> { static constexpr int NS = 4, BN = 64, BUFCOLS = 256, TMEM_COLS = 512; };
+template <> struct ModeCfg<0> { static constexpr int NS = 2, BN = 128, BUFCOLS = 128, TMEM_COLS = 256, STAGES = 3; };
+template <> struct ModeCfg<1> { static constexpr int NS = 4, BN = 64, BUFCOLS = 256, TMEM_COLS = 512, STAGES = 2; };
 
 // One K segment: chunks over layers t < T and inner offsets j0 < K step BK.
 struct KSeg {
