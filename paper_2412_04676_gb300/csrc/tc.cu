@@ -420,8 +420,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         for (int v = et; v < BM * vpr; v += EPI_THREADS) {
                             const int r = v / vpr, cv = v % vpr;
                             const int grow = w.m0 + r, gcol = w.n0 + cv * 8;
-                            if (grow >= w.M || gcol >= ldo) continue;
-                            *reinterpret_cast<uint4*>(o0 + q * w.plane + grow * ldo + gcol) =
+                            if (grow >= w.M || gcol >= w.colcap) continue;
+                            long long at = (long long)grow * ldo + gcol;
+                            if (w.lay_rows > 0) {
+                                const int t = grow / w.lay_rows;
+                                at = (long long)(grow - t * w.lay_rows) * ldo + t * w.lay_pitch + gcol;
+                            }
+                            *reinterpret_cast<uint4*>(o0 + q * w.plane + at) =
                                 *reinterpret_cast<const uint4*>(epi + r * K_::RS + ((cv ^ (r & (vpr - 1))) << 4));
                         }
                     }
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         for (int v = et; v < BM * vpr; v += EPI_THREADS) {
                             const int r = v / vpr, c8 = (v % vpr) * 8;
                             const int grow = w.m0 + r, gcol = w.n0 + c8;
-                            if (grow >= w.M || gcol >= ldo) continue;
+                            if (grow >= w.M || gcol >= w.colcap) continue;
                             *reinterpret_cast<uint4*>(o0 + q * w.plane + grow * ldo + gcol) =
                                 *reinterpret_cast<const uint4*>(epi + r * K_::RS + (((c8 >> 3) ^ (r & (vpr - 1))) << 4));
                         }
@@ -506,6 +511,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
 // block) unit (G = 32, or 8 / 16 for short rows, so a warp then covers
 // several rows).  GB300's FP64 pipe is narrow, so the per-element work is
 // integer and FP32 arithmetic on the FP64 bit patterns.
+// Output rows can be regrouped (a layer-stacked block stored with its layers
+// side by side along the row) through R, lpitch and rpitch.
 //   MODE 0: x = hi + lo, hi = bf16(f), lo = bf16(f - hi) with f = fp32(x)
 //     (|x - hi - lo| <= 2^-18 |x|).
 //   MODE 1: error-free slicing: with 2^(e-1) <= max |x| < 2^e over the unit,
@@ -518,8 +525,10 @@ struct SplitDesc {
     long long rs, cs;
     long long rows;
     int cols, ldd;
-    __nv_bfloat16* dst;
+    __nv_bfloat16* dst;  // source row r goes to dst + (r / R) * lpitch + (r % R) * rpitch
     long long plane;
+    long long R, lpitch, rpitch;
+    long long rbase;     // row index of src row 0 within the whole block (for the regrouping)
 };
 
 __device__ __forceinline__ float pow2f(int e) {
@@ -551,7 +560,8 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
             const int c = c0 + gl + G * h;
             bits[h] = (uv && c < b.cols && c < c0 + 64) ? src[r * b.rs + (long long)c * b.cs] : 0ULL;
         }
-        __nv_bfloat16* d = b.dst + r * b.ldd;
+        const long long ra = b.rbase + r;
+        __nv_bfloat16* d = b.dst + (ra / b.R) * b.lpitch + (ra % b.R) * b.rpitch;
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -723,6 +733,7 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
     T.blk_x.ensure(size_t(std::max(xt, 1LL)) * 8);
     T.blk_a.clear();
     T.blk_b.clear();
+    const int Tn = int(H.OL.cls[c0].states.size());
     for (int side = 0; side < 2; ++side) {
         const OpSet& O = side == 0 ? H.OL : H.OR;
         __nv_bfloat16* base = side == 0 ? P.ol.as<__nv_bfloat16>() : P.orr.as<__nv_bfloat16>();
@@ -730,10 +741,17 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
         const auto& off = side == 0 ? offL : offR;
         for (size_t i = 0; i < O.cls[c0].blocks.size(); ++i) {
             const OpBlock& bb = O.cls[c0].blocks[i];
-            const long long per = (long long)bb.rows * pad8(bb.cols);
+            const long long ldk = pad8(bb.cols);
+            const long long per = (long long)bb.rows * ldk;
             for (int k = 0; k < 2; ++k)
-                for (int q = 0; q < 2; ++q)
-                    GBD_CHECK_CUDA(cudaMemsetAsync(base + q * plane + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+                for (int q = 0; q < 2; ++q) {
+                    if (side == 0) {  // layer-stacked
+                        GBD_CHECK_CUDA(cudaMemsetAsync(base + q * plane + off[c0][i] + lay[k] * per, 0, size_t(per) * 2, st));
+                    } else if (bb.rows > 0) {  // layers side by side along each row
+                        GBD_CHECK_CUDA(cudaMemset2DAsync(base + q * plane + off[c0][i] + lay[k] * ldk, size_t(Tn * ldk) * 2, 0,
+                                                         size_t(ldk) * 2, size_t(bb.rows), st));
+                    }
+                }
         }
     }
     for (size_t q = 0; q < H.sq.size(); ++q) {
@@ -796,20 +814,27 @@ template <int MODE> void build_plan(Ctx& C) {
     {
         DevBuf d;
         std::vector<SplitDesc> sd;
-        auto add = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& dst, long long plane) {
+        // concat: layers side by side along each row ([row][layer][col]), the
+        // BF16x3 phase-2 B operand; otherwise layer-stacked rows
+        auto add = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& dst, long long plane,
+                       bool concat) {
             for (size_t c = 0; c < O.cls.size(); ++c)
                 for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
                     const OpBlock& b = O.cls[c].blocks[i];
-                    const long long rows = (long long)O.cls[c].states.size() * b.rows;
+                    const long long Tn = (long long)O.cls[c].states.size();
+                    const long long rows = Tn * b.rows;
                     const int ldd = pad8(b.cols);
                     const long long per = std::max<long long>(1, kSplitUnits / ((ldd + 63) / 64));
-                    for (long long r0 = 0; r0 < rows; r0 += per)
-                        sd.push_back({O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
-                                      b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i] + r0 * ldd, plane});
+                    for (long long r0 = 0; r0 < rows; r0 += per) {
+                        SplitDesc q{O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
+                                    b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i], plane, 1LL << 62, 0, ldd, r0};
+                        if (concat) { q.R = std::max(b.rows, 1); q.lpitch = ldd; q.rpitch = Tn * ldd; }
+                        sd.push_back(q);
+                    }
                 }
         };
-        add(H.OL, offL, P.ol, P.nL);
-        add(H.OR, offR, P.orr, P.nR);
+        add(H.OL, offL, P.ol, P.nL, false);
+        add(H.OR, offR, P.orr, P.nR, MODE == 0);
         if (!sd.empty()) {
             upload_vec(d, sd, st);
             for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
@@ -835,7 +860,7 @@ template <int MODE> void build_plan(Ctx& C) {
             const long long per = std::max<long long>(1, 32 / ((ps.ldp + 63) / 64));
             for (long long r0 = 0; r0 < ps.mR; r0 += per)
                 sd.push_back({H.xin.as<double>() + ps.src + r0, 1, ps.mR, std::min<long long>(per, ps.mR - r0), ps.mL,
-                              ps.ldp, P.psi.as<__nv_bfloat16>() + ps.dst + r0 * ps.ldp, P.np});
+                              ps.ldp, P.psi.as<__nv_bfloat16>() + ps.dst, P.np, 1LL << 62, 0, ps.ldp, r0});
         }
         upload_vec(P.psi_split, sd, st);
         P.n_psi = int(sd.size());
@@ -901,17 +926,35 @@ template <int MODE> void build_plan(Ctx& C) {
                 w.c1 = s1[sidx].nchunk;
                 w.out_kind = 1;
                 w.promote = MODE == 0 ? (1 << 30) : 1;
-                w.ldo = pad8(mRi);
                 w.plane = P.nx;
+                w.colcap = pad8(mRi);
+                if (MODE == 0) {  // X stored [row][layer][col] for the concatenated phase-2 K
+                    w.lay_rows = mLo;
+                    w.lay_pitch = pad8(mRi);
+                    w.ldo = (long long)Tn * pad8(mRi);
+                } else {
+                    w.lay_rows = 0;
+                    w.ldo = pad8(mRi);
+                }
                 w.out = P.x.as<__nv_bfloat16>() + p.x;
                 w1.push_back(w);
             }
-        // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn
-        int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
         const long long orr = offR[p.c][p.br];
-        int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi), TBN);
         seg_of_out[p.so].push_back(int(s2.size()));
-        s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
+        if (MODE == 0) {
+            // phase 2 operands with layers side by side: X (mLo x Tn*ldk),
+            // OR (mRo x Tn*ldk); one K of Tn * ldk, padded only at its end
+            const int Kc = Tn * pad8(mRi);
+            int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, Kc, mLo, 0, Kc, 0, BM);
+            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, Kc, mRo, 0, Kc, 0, TBN);
+            s2.push_back({mX, mO, 0, 0, Kc, 1, 2, (Kc + BK - 1) / BK});
+        } else {
+            // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn; K
+            // chunks stay inside one layer (the slices' grid is per layer row)
+            int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
+            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi), TBN);
+            s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
+        }
     }
     // phase 2 work: per output sector tile, K split into near-equal chunk ranges
     long long total_chunks = 0;
@@ -954,6 +997,7 @@ template <int MODE> void build_plan(Ctx& C) {
                     w.out_kind = 0;
                     w.promote = MODE == 0 ? 8 : 1;
                     w.ldo = TBN;
+                    w.colcap = TBN;
                     w.out = reinterpret_cast<void*>(npart);  // patched to a pointer below
                     w2.push_back(w);
                     ++npart;

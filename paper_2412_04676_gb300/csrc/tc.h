@@ -57,8 +57,13 @@ struct Work {
     int c0, c1;        // chunk range over the concatenated segments
     int out_kind;      // 0: FP32-pair partial tile, 1: BF16 slice planes, 2: FP64 matrix
     int promote;       // chunks between promotions of the TMEM accumulators
-    long long ldo;
+    long long ldo;     // output row pitch (elements)
     long long plane;   // element distance between BF16 slice planes (kind 1)
+    // kind 1 with layer-concatenated output: output row t * lay_rows + r goes
+    // to row r at column offset t * lay_pitch (lay_rows = 0: plain rows)
+    int lay_rows;
+    int colcap;        // kind 1: columns written per row (per layer)
+    long long lay_pitch;
     void* out;
 };
 
