@@ -32,7 +32,10 @@ namespace tc {
 
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
 
-template <int MODE> struct KT {
+// PH 1: phase-1 kernel (BF16 output planes through a staging tile); PH 2:
+// phase-2 kernel (split-K partial tiles straight from registers, so its
+// shared memory goes to pipeline stages).
+template <int MODE, int PH> struct KT {
     static constexpr int NS = ModeCfg<MODE>::NS;
     static constexpr int BN = ModeCfg<MODE>::BN;
     static constexpr int BUFCOLS = ModeCfg<MODE>::BUFCOLS;
@@ -41,10 +44,11 @@ template <int MODE> struct KT {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
     static constexpr int CP = BN / 4;                        // accumulator columns per epilogue thread
-    static constexpr int ST = ModeCfg<MODE>::STAGES;
-    static constexpr int RS = BN * 2;                        // row stride of the BF16 staging tile (XOR-swizzled)
-    static constexpr int EPI_BYTES = BM * RS;                // one output plane at a time
-    static constexpr int RMAX_BYTES = MODE == 1 ? 4 * BM * 4 : 0;    // row maxima of the four column parts
+    static constexpr int ST = (PH == 2 && MODE == 0) ? 3 : 2;
+    static constexpr int RS = BN * 2;                        // row stride of a BF16 staging plane (XOR-swizzled)
+    static constexpr int NPL = PH == 1 ? (MODE == 0 ? 2 : 1) : 0;  // staging planes
+    static constexpr int EPI_BYTES = NPL * BM * RS;
+    static constexpr int RMAX_BYTES = (MODE == 1 && PH == 1) ? 4 * BM * 4 : 0;  // row maxima of the four column parts
     static constexpr int SMEM_BYTES = ST * STAGE_BYTES + EPI_BYTES + RMAX_BYTES + 1024;
     static_assert(ST <= MAX_STAGES, "barrier arrays");
     // instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN
@@ -170,11 +174,11 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     hi = sum;
 }
 
-template <int MODE>
+template <int MODE, int PH>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restrict__ works, int nworks,
                                                              const KSeg* __restrict__ segs,
                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
-    using K_ = KT<MODE>;
+    using K_ = KT<MODE, PH>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
@@ -355,7 +359,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         uint32_t r[16];
                         tmem_ld16(tb + c * 16, r);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) two_sum_acc(ah[c * 16 + i], al[c * 16 + i], __uint_as_float(r[i]));
+                        for (int i = 0; i < 16; ++i) {
+                            // phase 1 drains once (K = one block dimension): plain FP32
+                            if constexpr (PH == 1) ah[c * 16 + i] += __uint_as_float(r[i]);
+                            else two_sum_acc(ah[c * 16 + i], al[c * 16 + i], __uint_as_float(r[i]));
+                        }
                     }
                 } else {
                     // order 1 and order 2 are exact FP32 sums; orders 3-4 are
@@ -376,29 +384,27 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             }
             if (abort_s) break;
             const Work w = works[wi];  // loaded after the drains: keeps registers free for ah / al
-            const int gr = w.m0 + row;
-            const int gc0 = w.n0 + part * CP;
-            if (w.out_kind == 0) {
+            if constexpr (PH == 2) {
                 // partial tile of (hi, lo) pairs, column-pair-major: a warp
                 // writes 512 contiguous bytes per store
                 float4* out = reinterpret_cast<float4*>(w.out);
 #pragma unroll
                 for (int i = 0; i < CP; i += 2)
                     out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
-            } else if (w.out_kind == 1) {
+            } else {
                 __nv_bfloat16* o0 = reinterpret_cast<__nv_bfloat16*>(w.out);
                 const long long ldo = w.ldo;
                 const int et = threadIdx.x - 64;  // 0 .. EPI_THREADS - 1
                 constexpr int vpr = K_::BN / 8;   // 16-byte vectors per row
                 if constexpr (MODE == 0) {
-                    // BF16 hi / lo, one plane at a time through the staging
-                    // tile (16-byte vectors XOR-swizzled by row), then
-                    // coalesced 16-byte stores of whole rows
+                    // BF16 hi / lo through two staging planes (16-byte
+                    // vectors XOR-swizzled by row), then coalesced 16-byte
+                    // stores of whole rows
                     uint32_t ph[CP / 2], pl[CP / 2];
 #pragma unroll
                     for (int i = 0; i < CP; i += 2) {
                         // x - bf16(x) is exact in FP32, so the split needs no FP64
-                        const float x0 = ah[i] + al[i], x1 = ah[i + 1] + al[i + 1];
+                        const float x0 = ah[i], x1 = ah[i + 1];  // phase 1: no lo part
                         const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
                         const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
                         const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
@@ -406,28 +412,41 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         ph[i / 2] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
                         pl[i / 2] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
                     }
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // earlier readers are done
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const uint32_t* pk = q == 0 ? ph : pl;
-                        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // earlier readers are done
-#pragma unroll
-                        for (int j = 0; j < CP / 8; ++j) {
-                            const int v = part * (CP / 8) + j;
-                            *reinterpret_cast<uint4*>(epi + row * K_::RS + ((v ^ (row & (vpr - 1))) << 4)) =
-                                make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    for (int j = 0; j < CP / 8; ++j) {
+                        const int v = part * (CP / 8) + j;
+                        const int off = row * K_::RS + ((v ^ (row & (vpr - 1))) << 4);
+                        *reinterpret_cast<uint4*>(epi + off) = make_uint4(ph[4 * j], ph[4 * j + 1], ph[4 * j + 2], ph[4 * j + 3]);
+                        *reinterpret_cast<uint4*>(epi + BM * K_::RS + off) =
+                            make_uint4(pl[4 * j], pl[4 * j + 1], pl[4 * j + 2], pl[4 * j + 3]);
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                    // thread et copies vector et % vpr of rows et / vpr + k * rstep;
+                    // with layer-concatenated output, row t * lay_rows + rr goes
+                    // to row rr at column offset t * lay_pitch
+                    constexpr int rstep = EPI_THREADS / vpr;
+                    const int cv = et % vpr;
+                    const int gcol = w.n0 + cv * 8;
+                    int r = et / vpr;
+                    int grow = w.m0 + r;
+                    int t = 0, rr = grow;
+                    if (w.lay_rows > 0) {
+                        t = grow / w.lay_rows;
+                        rr = grow - t * w.lay_rows;
+                    }
+                    for (; r < BM; r += rstep) {
+                        if (grow < w.M && gcol < w.colcap) {
+                            const long long at = w.lay_rows > 0 ? (long long)rr * ldo + (long long)t * w.lay_pitch + gcol
+                                                                : (long long)grow * ldo + gcol;
+                            const int so = r * K_::RS + ((cv ^ (r & (vpr - 1))) << 4);
+                            *reinterpret_cast<uint4*>(o0 + at) = *reinterpret_cast<const uint4*>(epi + so);
+                            *reinterpret_cast<uint4*>(o0 + w.plane + at) = *reinterpret_cast<const uint4*>(epi + BM * K_::RS + so);
                         }
-                        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-                        for (int v = et; v < BM * vpr; v += EPI_THREADS) {
-                            const int r = v / vpr, cv = v % vpr;
-                            const int grow = w.m0 + r, gcol = w.n0 + cv * 8;
-                            if (grow >= w.M || gcol >= w.colcap) continue;
-                            long long at = (long long)grow * ldo + gcol;
-                            if (w.lay_rows > 0) {
-                                const int t = grow / w.lay_rows;
-                                at = (long long)(grow - t * w.lay_rows) * ldo + t * w.lay_pitch + gcol;
-                            }
-                            *reinterpret_cast<uint4*>(o0 + q * w.plane + at) =
-                                *reinterpret_cast<const uint4*>(epi + r * K_::RS + ((cv ^ (r & (vpr - 1))) << 4));
+                        grow += rstep;
+                        if (w.lay_rows > 0) {
+                            rr += rstep;
+                            while (rr >= w.lay_rows) { rr -= w.lay_rows; ++t; }
                         }
                     }
                 } else {
@@ -486,13 +505,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                                 *reinterpret_cast<const uint4*>(epi + r * K_::RS + (((c8 >> 3) ^ (r & (vpr - 1))) << 4));
                         }
                     }
-                }
-            } else {
-                if (gr < w.M) {
-                    double* o = reinterpret_cast<double*>(w.out) + (long long)gr * w.ldo;
-#pragma unroll
-                    for (int i = 0; i < CP; ++i)
-                        if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
                 }
             }
         }
@@ -797,8 +809,7 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
 
 // Slice planes, tensor maps and work lists of one product form.
 template <int MODE> void build_plan(Ctx& C) {
-    using K_ = KT<MODE>;
-    constexpr int NS = K_::NS, TBN = K_::BN;
+    constexpr int NS = ModeCfg<MODE>::NS, TBN = ModeCfg<MODE>::BN;
     Heff& H = C.H;
     TcHeff& T = H.tc;
     TcPlan& P = T.pl[MODE];
@@ -1032,8 +1043,10 @@ template <int MODE> void build_plan(Ctx& C) {
     P.n_w1 = int(w1.size());
     P.n_w2 = int(w2.size());
     P.n_red = int(red.size());
-    GBD_CHECK_CUDA(
-        cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, K_::SMEM_BYTES));
+    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        KT<MODE, 1>::SMEM_BYTES));
+    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        KT<MODE, 2>::SMEM_BYTES));
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));
     P.built = true;
     C.timers[Ctx::T_PREP_SPLIT] += t1 - t0;
@@ -1082,7 +1095,6 @@ void tc_prepare(Ctx& C, int mode) {
 
 namespace {
 template <int MODE> void run_plan(Ctx& C) {
-    using K_ = KT<MODE>;
     Heff& H = C.H;
     TcHeff& T = H.tc;
     TcPlan& P = T.pl[MODE];
@@ -1092,13 +1104,13 @@ template <int MODE> void run_plan(Ctx& C) {
         count_launch();
     }
     if (P.n_w1 > 0) {
-        tc_gemm_kernel<MODE><<<std::min(P.n_w1, T.n_sm), THREADS, K_::SMEM_BYTES, st>>>(
+        tc_gemm_kernel<MODE, 1><<<std::min(P.n_w1, T.n_sm), THREADS, KT<MODE, 1>::SMEM_BYTES, st>>>(
             P.w1.as<Work>(), P.n_w1, P.s1.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
         count_launch();
     }
     if (P.n_red > 0) {
         if (P.n_w2 > 0) {
-            tc_gemm_kernel<MODE><<<std::min(P.n_w2, T.n_sm), THREADS, K_::SMEM_BYTES, st>>>(
+            tc_gemm_kernel<MODE, 2><<<std::min(P.n_w2, T.n_sm), THREADS, KT<MODE, 2>::SMEM_BYTES, st>>>(
                 P.w2.as<Work>(), P.n_w2, P.s2.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
             count_launch();
         }
