@@ -628,19 +628,25 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
 
 // partial tiles hold FP32 (hi, lo) pairs, column-pair-major: element (i, j)
 // at pair index ((j / 2) * BM + i) * 2 + (j % 2)
+// grid (tiles, kReduceSplit): CTA y sums rows y, y + kReduceSplit, ... of its tile
+constexpr int kReduceSplit = 16;
+
 __global__ void reduce_kernel(const Reduce* __restrict__ red, const float2* __restrict__ partial) {
     const Reduce r = red[blockIdx.x];
-    for (int e = threadIdx.x; e < BM * r.bn; e += blockDim.x) {
-        const int i = e / r.bn, j = e % r.bn;
-        const int gi = r.m0 + i, gj = r.n0 + j;
-        if (gi >= r.M || gj >= r.N) continue;
-        const long long idx = ((long long)(j / 2) * BM + i) * 2 + (j % 2);
-        double v = 0.0;
-        for (int p = r.p0; p < r.p1; ++p) {
-            const float2 x = partial[(long long)p * BM * r.bn + idx];
-            v += double(x.x) + double(x.y);
+    for (int i = blockIdx.y; i < BM; i += kReduceSplit) {
+        const int gi = r.m0 + i;
+        if (gi >= r.M) break;
+        for (int j = threadIdx.x; j < r.bn; j += blockDim.x) {
+            const int gj = r.n0 + j;
+            if (gj >= r.N) break;
+            const long long idx = ((long long)(j / 2) * BM + i) * 2 + (j % 2);
+            double v = 0.0;
+            for (int p = r.p0; p < r.p1; ++p) {
+                const float2 x = partial[(long long)p * BM * r.bn + idx];
+                v += double(x.x) + double(x.y);
+            }
+            r.out[(long long)gi * r.ldo + gj] = v;
         }
-        r.out[(long long)gi * r.ldo + gj] = v;
     }
 }
 
@@ -1114,7 +1120,7 @@ template <int MODE> void run_plan(Ctx& C) {
                 P.w2.as<Work>(), P.n_w2, P.s2.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
             count_launch();
         }
-        reduce_kernel<<<P.n_red, 256, 0, st>>>(P.red.as<Reduce>(), P.partial.as<float2>());
+        reduce_kernel<<<dim3(P.n_red, kReduceSplit), 128, 0, st>>>(P.red.as<Reduce>(), P.partial.as<float2>());
         count_launch();
     }
     if (MODE == 0 && T.blk) {
