@@ -331,8 +331,10 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * product issues (ten slice products; not accumulated), then the host wall
  * time (ms) of the tensor-core operand preparation in three parts: operator
  * splitting, planning (work lists, tensor maps), upload, then the useful
- * GFLOP of the H_eff products in each of the three forms.  *n gets the
- * count; out may be NULL. */
+ * GFLOP of the H_eff products in each of the three forms, then the
+ * renormalisation and enlargement GFLOP run on the tensor cores in the
+ * sliced form (the FP64 GFLOP counters above count FP64 GEMMs only).  *n
+ * gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

@@ -354,7 +354,8 @@ class Context:
               "davidson_host", "enlarge_gflop", "renorm_gflop", "tc_issued_gflop_p1", "tc_issued_gflop_p2",
               "products_fp64_ms", "products_bf16x3_ms", "products_sliced_ms", "products_fp64_n", "products_bf16x3_n",
               "products_sliced_n", "tc_sliced_issued_gflop", "tc_prep_split", "tc_prep_plan", "tc_prep_upload",
-              "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop"]
+              "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop", "renorm_tc_gflop",
+              "enlarge_tc_gflop"]
 
     def timers(self):
         out = np.zeros(32)

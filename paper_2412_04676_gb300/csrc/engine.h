@@ -113,7 +113,8 @@ struct Ctx {
     // phase timers (ms): host planning and device execution
     enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2,
            T_PROD_MS0, T_PROD_MS1, T_PROD_MS2, T_PROD_N0, T_PROD_N1, T_PROD_N2, T_TC_ISSUE_SL,
-           T_PREP_SPLIT, T_PREP_PLAN, T_PREP_UPLOAD, T_PROD_GF0, T_PROD_GF1, T_PROD_GF2, T_COUNT };
+           T_PREP_SPLIT, T_PREP_PLAN, T_PREP_UPLOAD, T_PROD_GF0, T_PROD_GF1, T_PROD_GF2,
+           T_REN_TC_GFLOP, T_ENL_TC_GFLOP, T_COUNT };
     double timers[T_COUNT] = {0};
 };
 

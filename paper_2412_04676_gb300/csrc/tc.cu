@@ -34,7 +34,8 @@ constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // PH 1: phase-1 kernel (BF16 output planes through a staging tile); PH 2:
 // phase-2 kernel (split-K partial tiles straight from registers, so its
-// shared memory goes to pipeline stages).
+// shared memory goes to pipeline stages); PH 3: FP64 output tiles (one work
+// item per tile, no split-K).
 template <int MODE, int PH> struct KT {
     static constexpr int NS = ModeCfg<MODE>::NS;
     static constexpr int BN = ModeCfg<MODE>::BN;
@@ -44,7 +45,7 @@ template <int MODE, int PH> struct KT {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
     static constexpr int CP = BN / 4;                        // accumulator columns per epilogue thread
-    static constexpr int ST = (PH == 2 && MODE == 0) ? 3 : 2;
+    static constexpr int ST = (PH == 2 && MODE == 0) ? 3 : 2;  // PH 3: FP64 output straight from registers
     static constexpr int RS = BN * 2;                        // row stride of a BF16 staging plane (XOR-swizzled)
     static constexpr int NPL = PH == 1 ? (MODE == 0 ? 2 : 1) : 0;  // staging planes
     static constexpr int EPI_BYTES = NPL * BM * RS;
@@ -384,7 +385,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             }
             if (abort_s) break;
             const Work w = works[wi];  // loaded after the drains: keeps registers free for ah / al
-            if constexpr (PH == 2) {
+            if constexpr (PH == 3) {
+                const int gr = w.m0 + row;
+                const int gc0 = w.n0 + part * CP;
+                if (gr < w.M) {
+                    double* o = reinterpret_cast<double*>(w.out) + (long long)gr * w.ldo;
+#pragma unroll
+                    for (int i = 0; i < CP; ++i)
+                        if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
+                }
+            } else if constexpr (PH == 2) {
                 // partial tile of (hi, lo) pairs, column-pair-major: a warp
                 // writes 512 contiguous bytes per store
                 float4* out = reinterpret_cast<float4*>(w.out);
@@ -1135,6 +1145,114 @@ template <int MODE> void run_plan(Ctx& C) {
 void tc_apply(Ctx& C, int mode) {
     GBD_REQUIRE(C.H.tc_ready && C.H.tc.pl[mode].built, GBD_ERR_STATE, "tensor-core plan not prepared");
     if (mode == 0) run_plan<0>(C); else run_plan<1>(C);
+}
+
+// Phase A of the renormalisation (Sec. II.B step 3) on the tensor cores in the
+// sliced form: tmp (T*dimO x k_i) = O_stacked (T*dimO x dimI) U_i for every
+// kept block, with O read from the sliced planes of the current enlarged set
+// (built for the anchor products) and U_i^T sliced here.  tmp[j] starts at
+// tmp + toff[j] for the j-th block of out in class order.  Returns false
+// (nothing launched) when the sliced planes of O are not built.
+bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, const std::vector<long long>& toff,
+                       double* tmp) {
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    if (!H.tc_ready || !T.pl[1].built) return false;
+    const bool left = &O == &H.OL;
+    if (!left && &O != &H.OR) return false;
+    constexpr int NS = ModeCfg<1>::NS, TBN = ModeCfg<1>::BN;
+    TcPlan& P = T.pl[1];
+    cudaStream_t st = C.cs;
+    std::vector<std::vector<long long>> off;
+    op_layout(O, off);
+    const __nv_bfloat16* arena = left ? P.ol.as<__nv_bfloat16>() : P.orr.as<__nv_bfloat16>();
+    const long long plane = left ? P.nL : P.nR;
+    // U_Q^T per kept sector Q (k rows, K = basis dimension), sliced
+    std::vector<long long> uoff(U.out.q.size(), -1);
+    long long nu = 0;
+    for (size_t q = 0; q < U.out.q.size(); ++q) {
+        if (U.off[q] < 0) continue;
+        const int e = U.basis.find(U.out.q[q]);
+        uoff[q] = nu;
+        nu += (long long)U.out.dim[q] * pad8(U.basis.dim[e]);
+    }
+    nu = std::max(nu, 8LL);
+    T.ren_u.ensure(size_t(nu) * NS * 2);
+    std::vector<SplitDesc> sd;
+    for (size_t q = 0; q < U.out.q.size(); ++q) {
+        if (uoff[q] < 0) continue;
+        const int k = U.out.dim[q];
+        const int dim = U.basis.dim[U.basis.find(U.out.q[q])];
+        // element (r = kept state, c = basis state) of U^T is U[c][r]
+        const long long per = std::max<long long>(1, 32 / ((pad8(dim) + 63) / 64));
+        for (long long r0 = 0; r0 < k; r0 += per)
+            sd.push_back({U.data.as<double>() + U.off[q] + r0, 1, k, std::min<long long>(per, k - r0), dim, pad8(dim),
+                          T.ren_u.as<__nv_bfloat16>() + uoff[q], nu, 1LL << 62, 0, pad8(dim), r0});
+    }
+    DevBuf dsd;
+    upload_vec(dsd, sd, st);
+    if (!sd.empty()) {
+        split_kernel<1><<<unsigned(sd.size()), 256, 0, st>>>(dsd.as<SplitDesc>());
+        count_launch();
+    }
+    std::vector<CUtensorMap> maps;
+    std::vector<KSeg> segs;
+    std::vector<Work> works;
+    size_t j = 0;
+    for (size_t c = 0; c < out.cls.size(); ++c) {
+        const int Tn = int(out.cls[c].states.size());
+        for (const auto& nb : out.cls[c].blocks) {
+            const int eo = U.basis.find(nb.Qo), ei = U.basis.find(nb.Qi);
+            const int dimO = U.basis.dim[eo], dimI = U.basis.dim[ei];
+            int bi = -1;
+            for (size_t x = 0; x < O.cls[c].blocks.size(); ++x)
+                if (O.cls[c].blocks[x].qo == eo && O.cls[c].blocks[x].qi == ei) bi = int(x);
+            GBD_REQUIRE(bi >= 0, GBD_ERR_STATE, "renormalisation: missing enlarged block");
+            const int mA = int(maps.size());
+            maps.push_back(make_map(arena + off[c][bi], dimI, (long long)Tn * dimO, 0, pad8(dimI), 0, NS, plane, BM));
+            maps.push_back(make_map(T.ren_u.as<__nv_bfloat16>() + uoff[nb.qi], dimI, nb.cols, 0, pad8(dimI), 0, NS, nu,
+                                    TBN));
+            const int sidx = int(segs.size());
+            segs.push_back({mA, mA + 1, 0, 0, dimI, 1, 2, (dimI + BK - 1) / BK});
+            for (long long m0 = 0; m0 < (long long)Tn * dimO; m0 += BM)
+                for (int n0 = 0; n0 < nb.cols; n0 += TBN) {
+                    Work w{};
+                    w.m0 = int(m0);
+                    w.n0 = n0;
+                    w.M = Tn * dimO;
+                    w.N = nb.cols;
+                    w.seg0 = sidx;
+                    w.nseg = 1;
+                    w.c0 = 0;
+                    w.c1 = segs[sidx].nchunk;
+                    w.out_kind = 2;
+                    w.promote = 1;
+                    w.ldo = nb.cols;
+                    w.colcap = nb.cols;
+                    w.out = tmp + toff[j];
+                    works.push_back(w);
+                }
+            ++j;
+        }
+    }
+    if (works.empty()) return true;
+    auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
+    std::stable_sort(works.begin(), works.end(), longer);
+    DevBuf dmaps, dsegs, dworks;
+    upload_vec(dmaps, maps, st);
+    upload_vec(dsegs, segs, st);
+    upload_vec(dworks, works, st);
+    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        KT<1, 3>::SMEM_BYTES));
+    const int nw = int(works.size());
+    tc_gemm_kernel<1, 3><<<std::min(nw, T.n_sm), THREADS, KT<1, 3>::SMEM_BYTES, st>>>(
+        dworks.as<Work>(), nw, dsegs.as<KSeg>(), dmaps.as<CUtensorMap>(), T.err.as<int>());
+    count_launch();
+    GBD_CHECK_CUDA(cudaGetLastError());
+    GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the tables above are freed on return
+    const int e = tc_error(C);
+    GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core renormalisation stopped on a bounded wait (code " + std::to_string(e) + ")");
+    return true;
 }
 
 int tc_error(Ctx& C) {

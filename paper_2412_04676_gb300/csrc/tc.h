@@ -55,7 +55,7 @@ struct Work {
     int M, N;          // valid rows / cols of the whole output (bounds)
     int seg0, nseg;
     int c0, c1;        // chunk range over the concatenated segments
-    int out_kind;      // 0: FP32-pair partial tile, 1: BF16 slice planes, 2: FP64 matrix
+    int out_kind;      // 0: FP32-pair partial tile, 1: BF16 slice planes, 2: FP64 matrix (phase kernels 2, 1, 3)
     int promote;       // chunks between promotions of the TMEM accumulators
     long long ldo;     // output row pitch (elements)
     long long plane;   // element distance between BF16 slice planes (kind 1)
@@ -98,13 +98,19 @@ struct TcHeff {
     std::vector<PsiSec> psec;
     DevBuf err;                             // device error word
     int n_sm = 152;
+    DevBuf ren_u;                           // sliced U^T of the renormalisation
     GemmPlan blk_a, blk_b;                  // FP64 block-Hamiltonian terms (mode 0, optional)
     DevBuf blk_x;
     bool blk = false;
 };
 
+struct OpSet;
+struct Iso;
+
 void tc_prepare(Ctx& C, int mode);
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
+bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, const std::vector<long long>& toff,
+                       double* tmp);
 
 }  // namespace gbd

@@ -133,3 +133,27 @@ def test_sliced_product_full_size_config2():
     assert np.linalg.norm(ys - y64) <= 1e-8 * np.linalg.norm(y64)
     zs = ctx.apply_heff(b, z, precision=g.SLICED_BF16)
     assert abs(z @ ys - x @ zs) <= 1e-8 * np.linalg.norm(ys) * np.linalg.norm(z)
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+def test_sliced_renormalisation_matches_fp64(direction):
+    # the same two-site vector truncated in two contexts: FP64 renormalisation
+    # (mixed_polish=1) and phase A of it on the tensor cores in the sliced form
+    # (mixed_polish=2); the eigensolve is FP64 in both, so the kept bases agree
+    # and the renormalised environments differ by the sliced rounding only
+    L, N, tsz, D, b = 10, 10, 0, 80, 4
+    out = {}
+    for polish in (1, 2):
+        c = heff_case(L, N, tsz, D, 540, b, oracle=False, precision=g.MIXED_BF16X3, mixed_polish=polish)
+        ctx = c["ctx"]
+        secs, info = ctx.tables(b)
+        x = np.random.default_rng(7).normal(size=info["dim"])
+        x /= np.linalg.norm(x)
+        ctx.apply_heff(b, x, precision=g.SLICED_BF16)  # builds this position's sliced planes
+        ctx.set_psi(b, x)
+        ctx.truncate(b, direction, 40)
+        tm = ctx.timers()
+        assert (tm["renorm_tc_gflop"] > 0) == (polish == 2), tm  # the tensor-core path ran exactly when asked
+        out[polish] = ctx.env_export(0 if direction == 1 else 1, b + 1)
+    assert out[1].shape == out[2].shape and out[1].size > 0
+    assert np.linalg.norm(out[2] - out[1]) <= 1e-8 * np.linalg.norm(out[1])
