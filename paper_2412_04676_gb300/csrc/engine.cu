@@ -253,6 +253,12 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     P.clear();
     std::vector<CopyItem> items;
     std::vector<CopySrc> srcs;
+    // mixed form: the dense coefficient GEMMs run on the tensor cores in the
+    // sliced form (FP64 GEMMs otherwise)
+    const bool tc_env = C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2;
+    std::vector<TcEnlTask> tc_tasks;
+    std::vector<TcEnlSeg> tc_segs;
+    double tc_flops = 0.0;
     for (const auto& sub : subs) {
         const OpClass& oc = out.cls[sub.cls];
         const OpBlock& ob = oc.blocks[sub.blk];
@@ -268,6 +274,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         t.nbatch = 1;
         t.beta = 0.0;
         std::vector<GemmSeg> segs;
+        const int tc_seg0 = int(tc_segs.size());
         std::vector<std::pair<int, const OpBlock*>> sp;  // sparse links of this sub-block
         for (auto& pr : sub.src) {
             const Link& L = links[pr.first];
@@ -275,6 +282,11 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             const OpBlock& ib = ic.blocks[pr.second];
             if (sparse[pr.first]) {
                 sp.push_back({pr.first, &ib});
+                continue;
+            }
+            if (tc_env) {
+                tc_segs.push_back({dW + L.doff, int(ic.states.size()), Tout, din + ib.off, (long long)ib.rows * ib.cols});
+                tc_flops += 2.0 * Tout * double(t.N) * double(ic.states.size());
                 continue;
             }
             GemmSeg g{};
@@ -289,6 +301,8 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             g.coef = 1.0;
             segs.push_back(g);
         }
+        if (int(tc_segs.size()) > tc_seg0)
+            tc_tasks.push_back({dsub, t.ldc, t.ldr, t.M, t.N, t.ncols, tc_seg0, int(tc_segs.size()) - tc_seg0});
         if (!segs.empty()) P.add_task(t, segs);
         if (sp.empty()) continue;
         for (int c = 0; c < Tout; ++c) {
@@ -322,6 +336,19 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     C.timers[Ctx::T_ENL_GFLOP] += P.flops * 1e-9;
     P.upload(C.cs);
     P.launch(C.cs);
+    if (!tc_tasks.empty()) {
+        // bounds of the sliced GEMM outputs and inputs, checked like the FP64 plan's
+        for (const auto& tk : tc_tasks) {
+            const double* e = tk.C + (long long)(tk.M - 1) * tk.ldc + (long long)((tk.N - 1) / tk.ncols) * tk.ldr +
+                              (tk.N - 1) % tk.ncols;
+            GBD_REQUIRE(tk.C >= dout && e < dout + out.total, GBD_ERR_STATE, "enlarge: sliced output outside its block");
+        }
+        for (const auto& sg : tc_segs)
+            GBD_REQUIRE(sg.E >= din && sg.E + (long long)sg.Tin * sg.n <= din + Ein.total, GBD_ERR_STATE,
+                        "enlarge: sliced input outside the environment");
+        tc_enlarge_dense(C, tc_tasks, tc_segs);
+        C.timers[Ctx::T_ENL_TC_GFLOP] += tc_flops * 1e-9;
+    }
     if (!items.empty()) {
         C.scratch_items.ensure(items.size() * sizeof(CopyItem));
         C.scratch_srcs.ensure(std::max<size_t>(srcs.size(), 1) * sizeof(CopySrc));

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstring>
 
@@ -390,9 +391,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int gc0 = w.n0 + part * CP;
                 if (gr < w.M) {
                     double* o = reinterpret_cast<double*>(w.out) + (long long)gr * w.ldo;
+                    if (w.ncols > 0) {
+                        int q = gc0 / w.ncols, rcol = gc0 - q * w.ncols;
 #pragma unroll
-                    for (int i = 0; i < CP; ++i)
-                        if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
+                        for (int i = 0; i < CP; ++i) {
+                            if (gc0 + i < w.N) o[(long long)q * w.ldr + rcol] = double(ah[i]) + double(al[i]);
+                            if (++rcol == w.ncols) { rcol = 0; ++q; }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CP; ++i)
+                            if (gc0 + i < w.N) o[gc0 + i] = double(ah[i]) + double(al[i]);
+                    }
                 }
             } else if constexpr (PH == 2) {
                 // partial tile of (hi, lo) pairs, column-pair-major: a warp
@@ -1253,6 +1263,117 @@ bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, c
     const int e = tc_error(C);
     GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core renormalisation stopped on a bounded wait (code " + std::to_string(e) + ")");
     return true;
+}
+
+// Dense enlargement GEMMs in the sliced form: A = W^T (Tout x Tin) per
+// segment, B = E^T (n x Tin) per input block, both sliced (transposed) here;
+// one FP64 output tile per work item, written with the sub-block strides.
+void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::vector<TcEnlSeg>& segs) {
+    constexpr int NS = ModeCfg<1>::NS, TBN = ModeCfg<1>::BN;
+    cudaStream_t st = C.cs;
+    // distinct operands
+    std::map<const double*, std::pair<long long, int>> wmap, emap;  // -> (offset in the slice planes, index)
+    std::vector<const TcEnlSeg*> wlist, elist;
+    long long nw = 0, ne = 0;
+    for (const auto& sg : segs) {
+        if (!wmap.count(sg.W)) {
+            wmap[sg.W] = {nw, int(wlist.size())};
+            wlist.push_back(&sg);
+            nw += (long long)sg.Tout * pad8(sg.Tin);
+        }
+        if (!emap.count(sg.E)) {
+            emap[sg.E] = {ne, int(elist.size())};
+            elist.push_back(&sg);
+            ne += sg.n * pad8(sg.Tin);
+        }
+    }
+    nw = std::max(nw, 8LL);
+    ne = std::max(ne, 8LL);
+    C.env_sl_w.ensure(size_t(nw) * NS * 2);
+    C.env_sl_e.ensure(size_t(ne) * NS * 2);
+    C.env_err.ensure(sizeof(int));
+    GBD_CHECK_CUDA(cudaMemsetAsync(C.env_err.p, 0, sizeof(int), st));
+    // slicing: W^T row c = column c of W; E^T row e = column e of E
+    std::vector<SplitDesc> sd;
+    auto add = [&](const double* src, long long rows, int K, long long src_rowstep, __nv_bfloat16* dst, long long plane) {
+        const long long per = std::max<long long>(1, kSplitUnits / ((pad8(K) + 63) / 64));
+        for (long long r0 = 0; r0 < rows; r0 += per)
+            sd.push_back({src + r0, 1, src_rowstep, std::min(per, rows - r0), K, pad8(K), dst, plane, 1LL << 62, 0, pad8(K),
+                          r0});
+    };
+    for (const auto* sg : wlist)
+        add(sg->W, sg->Tout, sg->Tin, sg->Tout, C.env_sl_w.as<__nv_bfloat16>() + wmap[sg->W].first, nw);
+    for (const auto* sg : elist)
+        add(sg->E, sg->n, sg->Tin, sg->n, C.env_sl_e.as<__nv_bfloat16>() + emap[sg->E].first, ne);
+    DevBuf dsd;
+    upload_vec(dsd, sd, st);
+    for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
+        const unsigned n = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
+        split_kernel<1><<<n, 256, 0, st>>>(dsd.as<SplitDesc>() + i0);
+        count_launch();
+    }
+    // tensor maps (one per distinct operand), segments, work items
+    std::vector<CUtensorMap> maps;
+    std::vector<int> wmi(wlist.size()), emi(elist.size());
+    for (size_t i = 0; i < wlist.size(); ++i) {
+        wmi[i] = int(maps.size());
+        maps.push_back(make_map(C.env_sl_w.as<__nv_bfloat16>() + wmap[wlist[i]->W].first, wlist[i]->Tin, wlist[i]->Tout, 0,
+                                pad8(wlist[i]->Tin), 0, NS, nw, BM));
+    }
+    for (size_t i = 0; i < elist.size(); ++i) {
+        emi[i] = int(maps.size());
+        maps.push_back(make_map(C.env_sl_e.as<__nv_bfloat16>() + emap[elist[i]->E].first, elist[i]->Tin, elist[i]->n, 0,
+                                pad8(elist[i]->Tin), 0, NS, ne, TBN));
+    }
+    std::vector<KSeg> ks;
+    ks.reserve(segs.size());
+    for (const auto& sg : segs)
+        ks.push_back({wmi[wmap[sg.W].second], emi[emap[sg.E].second], 0, 0, sg.Tin, 1, 2, (sg.Tin + BK - 1) / BK});
+    std::vector<Work> works;
+    for (const auto& tk : tasks) {
+        int nchunk = 0;
+        for (int i = tk.seg0; i < tk.seg0 + tk.nseg; ++i) nchunk += ks[i].nchunk;
+        for (int m0 = 0; m0 < tk.M; m0 += BM)
+            for (int n0 = 0; n0 < tk.N; n0 += TBN) {
+                Work w{};
+                w.m0 = m0;
+                w.n0 = n0;
+                w.M = tk.M;
+                w.N = tk.N;
+                w.seg0 = tk.seg0;
+                w.nseg = tk.nseg;
+                w.c0 = 0;
+                w.c1 = nchunk;
+                w.out_kind = 2;
+                w.promote = 1;
+                w.ldo = tk.ldc;
+                w.ncols = tk.ncols;
+                w.ldr = tk.ldr;
+                w.out = tk.C;
+                works.push_back(w);
+            }
+    }
+    if (works.empty()) return;
+    auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
+    std::stable_sort(works.begin(), works.end(), longer);
+    DevBuf dmaps, dsegs, dworks;
+    upload_vec(dmaps, maps, st);
+    upload_vec(dsegs, ks, st);
+    upload_vec(dworks, works, st);
+    int dev = 0, nsm = 152;
+    GBD_CHECK_CUDA(cudaGetDevice(&dev));
+    GBD_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        KT<1, 3>::SMEM_BYTES));
+    const int nwk = int(works.size());
+    tc_gemm_kernel<1, 3><<<std::min(nwk, std::max(nsm, 1)), THREADS, KT<1, 3>::SMEM_BYTES, st>>>(
+        dworks.as<Work>(), nwk, dsegs.as<KSeg>(), dmaps.as<CUtensorMap>(), C.env_err.as<int>());
+    count_launch();
+    GBD_CHECK_CUDA(cudaGetLastError());
+    GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the tables above are freed on return
+    int e = 0;
+    GBD_CHECK_CUDA(cudaMemcpy(&e, C.env_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core enlargement stopped on a bounded wait (code " + std::to_string(e) + ")");
 }
 
 int tc_error(Ctx& C) {

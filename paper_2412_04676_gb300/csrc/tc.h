@@ -64,6 +64,9 @@ struct Work {
     int lay_rows;
     int colcap;        // kind 1: columns written per row (per layer)
     long long lay_pitch;
+    // kind 2: column e of a row goes to (e / ncols) * ldr + e % ncols (ncols = 0: e)
+    int ncols;
+    long long ldr;
     void* out;
 };
 
@@ -107,10 +110,18 @@ struct TcHeff {
 struct OpSet;
 struct Iso;
 
+// Dense enlargement GEMMs (Sec. II.B step 1) for the sliced tensor-core form:
+// C[c][e] = sum over segments of sum_a W[a][c] E[a][e], W: [Tin][Tout] and
+// E: [Tin][n] FP64 (device); element e of the output row c sits at
+// C + c * ldc + (e / ncols) * ldr + e % ncols.
+struct TcEnlSeg { const double* W; int Tin, Tout; const double* E; long long n; };
+struct TcEnlTask { double* C; long long ldc, ldr; int M, N, ncols; int seg0, nseg; };
+
 void tc_prepare(Ctx& C, int mode);
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
 bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, const std::vector<long long>& toff,
                        double* tmp);
+void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::vector<TcEnlSeg>& segs);
 
 }  // namespace gbd

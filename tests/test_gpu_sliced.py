@@ -157,3 +157,24 @@ def test_sliced_renormalisation_matches_fp64(direction):
         out[polish] = ctx.env_export(0 if direction == 1 else 1, b + 1)
     assert out[1].shape == out[2].shape and out[1].size > 0
     assert np.linalg.norm(out[2] - out[1]) <= 1e-8 * np.linalg.norm(out[1])
+
+
+def test_sliced_enlargement_matches_fp64():
+    # the environments and enlarged blocks of one position built in two
+    # contexts: FP64 coefficient GEMMs (mixed_polish=1) and the same GEMMs on
+    # the tensor cores in the sliced form (mixed_polish=2).  The FP64 H_eff
+    # product then differs only through the enlargement's sliced rounding.
+    L, N, tsz, D, b = 10, 10, 0, 120, 4
+    ys = {}
+    for polish in (1, 2):
+        c = heff_case(L, N, tsz, D, 550, b, oracle=(polish == 1), precision=g.MIXED_BF16X3, mixed_polish=polish)
+        ctx = c["ctx"]
+        secs, info = ctx.tables(b)
+        x = np.random.default_rng(9).normal(size=info["dim"])
+        ys[polish] = ctx.apply_heff(b, x, precision=g.FP64)
+        tm = ctx.timers()
+        assert (tm["enlarge_tc_gflop"] > 0) == (polish == 2), tm
+        if polish == 1:
+            y_ref = c["He"].matvec(x)
+            assert np.linalg.norm(ys[1] - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    assert np.linalg.norm(ys[2] - ys[1]) <= 1e-8 * np.linalg.norm(ys[1])
