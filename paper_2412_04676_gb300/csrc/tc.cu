@@ -152,6 +152,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// MMA width of a work item: its valid columns rounded up to 16, at most BN
+template <int BN_> __device__ __forceinline__ int tile_n_of(int N, int n0) {
+    const int v = N - n0;
+    return v >= BN_ ? BN_ : ((v + 15) & ~15);
+}
+
 // position (segment, layer, inner offset) of global chunk c
 __device__ __forceinline__ void locate(const KSeg* segs, int seg0, int nseg, int c, int& s, int& t, int& j0) {
     s = seg0;
@@ -181,6 +187,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                                                              const KSeg* __restrict__ segs,
                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
     using K_ = KT<MODE, PH>;
+    auto tile_n = [](const Work& w) { return tile_n_of<K_::BN>(w.N, w.n0); };
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base_s;
@@ -269,6 +276,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             const int n = w.c1 - w.c0;
             if (n <= 0) continue;
             const int promote = w.promote > 0 ? w.promote : (1 << 30);
+            // MMA width: the tile's valid columns rounded up to 16 (M = 128 needs N % 16 == 0)
+            const uint32_t idesc = (K_::IDESC & ~(0x3Fu << 17)) | (uint32_t(tile_n(w) >> 3) << 17);
             int inbuf = 0;
             for (int i = 0; i < n; ++i, ++g) {
                 const int st = int(g % K_::ST);
@@ -298,9 +307,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                     if constexpr (MODE == 0) {
                         const uint64_t ah = sdesc(a0 + off), al = sdesc(a0 + K_::A_BYTES + off);
                         const uint64_t bh = sdesc(b0 + off), bl = sdesc(b0 + K_::B_BYTES + off);
-                        umma(d, ah, bh, K_::IDESC, acc);
-                        umma(d, ah, bl, K_::IDESC, 1u);
-                        umma(d, al, bh, K_::IDESC, 1u);
+                        umma(d, ah, bh, idesc, acc);
+                        umma(d, ah, bl, idesc, 1u);
+                        umma(d, al, bh, idesc, 1u);
                     } else {
                         // slice products by order: a1 b1 | a1 b2 + a2 b1 | orders 3 and 4
                         uint64_t sa[4], sb[4];
@@ -310,16 +319,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                             sb[q] = sdesc(b0 + q * K_::B_BYTES + off);
                         }
                         const uint32_t d2 = d + 64, d3 = d + 128;
-                        umma(d, sa[0], sb[0], K_::IDESC, acc);
-                        umma(d2, sa[0], sb[1], K_::IDESC, acc);
-                        umma(d2, sa[1], sb[0], K_::IDESC, 1u);
-                        umma(d3, sa[0], sb[2], K_::IDESC, acc);
-                        umma(d3, sa[1], sb[1], K_::IDESC, 1u);
-                        umma(d3, sa[2], sb[0], K_::IDESC, 1u);
-                        umma(d3, sa[0], sb[3], K_::IDESC, 1u);
-                        umma(d3, sa[1], sb[2], K_::IDESC, 1u);
-                        umma(d3, sa[2], sb[1], K_::IDESC, 1u);
-                        umma(d3, sa[3], sb[0], K_::IDESC, 1u);
+                        umma(d, sa[0], sb[0], idesc, acc);
+                        umma(d2, sa[0], sb[1], idesc, acc);
+                        umma(d2, sa[1], sb[0], idesc, 1u);
+                        umma(d3, sa[0], sb[2], idesc, acc);
+                        umma(d3, sa[1], sb[1], idesc, 1u);
+                        umma(d3, sa[2], sb[0], idesc, 1u);
+                        umma(d3, sa[0], sb[3], idesc, 1u);
+                        umma(d3, sa[1], sb[2], idesc, 1u);
+                        umma(d3, sa[2], sb[1], idesc, 1u);
+                        umma(d3, sa[3], sb[0], idesc, 1u);
                     }
                 }
                 umma_commit(smem_u32(&empty_bar[st]));
@@ -341,11 +350,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         const int row = quad * 32 + lane;
         int D = 0;
         for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
-            int ndrain;
+            int ndrain, nn;
             {
                 const int n = works[wi].c1 - works[wi].c0;
                 const int promote = works[wi].promote > 0 ? works[wi].promote : (1 << 30);
                 ndrain = n > 0 ? (n + promote - 1) / promote : 0;
+                nn = tile_n_of<K_::BN>(works[wi].N, works[wi].n0);  // TMEM columns the MMAs wrote
             }
             float ah[CP], al[CP];
 #pragma unroll
@@ -358,6 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 if constexpr (MODE == 0) {
 #pragma unroll
                     for (int c = 0; c < CP / 16; ++c) {
+                        if (part * CP + c * 16 >= nn) continue;  // warp-uniform: columns the MMAs did not write
                         uint32_t r[16];
                         tmem_ld16(tb + c * 16, r);
 #pragma unroll
@@ -370,14 +381,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 } else {
                     // order 1 and order 2 are exact FP32 sums; orders 3-4 are
                     // 2^-16 of order 1, so one rounded add joins them to order 2
-                    uint32_t r1[16], r2[16], r3[16];
-                    tmem_ld16(tb, r1);
-                    tmem_ld16(tb + 64, r2);
-                    tmem_ld16(tb + 128, r3);
+                    if (part * CP < nn) {  // warp-uniform: columns the MMAs wrote
+                        uint32_t r1[16], r2[16], r3[16];
+                        tmem_ld16(tb, r1);
+                        tmem_ld16(tb + 64, r2);
+                        tmem_ld16(tb + 128, r3);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        two_sum_acc(ah[i], al[i], __uint_as_float(r1[i]));
-                        two_sum_acc(ah[i], al[i], __uint_as_float(r2[i]) + __uint_as_float(r3[i]));
+                        for (int i = 0; i < 16; ++i) {
+                            two_sum_acc(ah[i], al[i], __uint_as_float(r1[i]));
+                            two_sum_acc(ah[i], al[i], __uint_as_float(r2[i]) + __uint_as_float(r3[i]));
+                        }
                     }
                 }
                 tc_fence_before();
@@ -1045,11 +1058,15 @@ template <int MODE> void build_plan(Ctx& C) {
     }
     P.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2));
     for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
-    // tensor-core work issued per product (whole tiles, every slice product):
-    // the gap to the useful flops is padding
+    // tensor-core work issued per product (whole 128-row tiles at the MMA
+    // width, every slice product): the gap to the useful flops is padding
     auto issued = [](const std::vector<Work>& ws) {
         double f = 0.0;
-        for (const auto& w : ws) f += double(w.c1 - w.c0) * BM * TBN * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
+        for (const auto& w : ws) {
+            const int v = w.N - w.n0;
+            const int nn = v >= TBN ? TBN : ((v + 15) & ~15);  // the kernel's MMA width
+            f += double(w.c1 - w.c0) * BM * nn * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
+        }
         return f * 1e-9;
     };
     P.issued_p1 = issued(w1);
