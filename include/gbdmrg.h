@@ -333,7 +333,10 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * splitting, planning (work lists, tensor maps), upload, then the useful
  * GFLOP of the H_eff products in each of the three forms, then the
  * renormalisation and enlargement GFLOP run on the tensor cores in the
- * sliced form (the FP64 GFLOP counters above count FP64 GEMMs only).  *n
+ * sliced form (the FP64 GFLOP counters above count FP64 GEMMs only), then
+ * the device time (ms, compute stream, host gaps included) of the phases of
+ * gbd_step: environments resident, enlargement, Davidson, density matrices
+ * and eigensolves, renormalisation, next start vector, IO scheduling.  *n
  * gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

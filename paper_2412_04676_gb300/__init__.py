@@ -355,12 +355,13 @@ class Context:
               "products_fp64_ms", "products_bf16x3_ms", "products_sliced_ms", "products_fp64_n", "products_bf16x3_n",
               "products_sliced_n", "tc_sliced_issued_gflop", "tc_prep_split", "tc_prep_plan", "tc_prep_upload",
               "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop", "renorm_tc_gflop",
-              "enlarge_tc_gflop"]
+              "enlarge_tc_gflop", "step_resident", "step_enlarge", "step_davidson", "step_rho_eig", "step_renorm",
+              "step_next", "step_io"]
 
     def timers(self):
-        out = np.zeros(32)
+        out = np.zeros(64)
         n = C.c_int()
-        _check(lib().gbd_timers(self.h, _ptr(out), 32, C.byref(n)))
+        _check(lib().gbd_timers(self.h, _ptr(out), 64, C.byref(n)))
         return dict(zip(self.TIMERS, out[:n.value]))
 
     def io_stats(self):

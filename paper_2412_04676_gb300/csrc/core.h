@@ -130,22 +130,44 @@ struct OpClass {
     }
 };
 
+// Cache of device blocks for the large per-position buffers (enlarged
+// operator arenas, tensor-core slice planes): every position allocates blocks
+// of similar sizes, and cudaFree synchronises the device and unmaps memory.
+// A released block keeps an event recorded on the stream that used it; the
+// next user's stream waits for that event, so reuse needs no host wait.
+void* devcache_get(size_t n, cudaStream_t st, size_t* got);
+void devcache_put(void* p, size_t bytes, cudaStream_t st);  // never throws
+void devcache_trim();                                        // cudaFree every cached block
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t cst = nullptr;  // stream of a cached block's users
+    bool cached = false;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), cst(o.cst), cached(o.cached) {
+        o.p = nullptr; o.bytes = 0; o.cst = nullptr; o.cached = false;
+    }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; cst = o.cst; cached = o.cached;
+            o.p = nullptr; o.bytes = 0; o.cst = nullptr; o.cached = false;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (cached) devcache_put(p, bytes, cst);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        cst = nullptr;
+        cached = false;
     }
     void ensure(size_t n) {  // grow-only, contents not kept
         if (n <= bytes && p) return;
@@ -153,6 +175,15 @@ struct DevBuf {
         if (n == 0) n = 16;
         GBD_CHECK_CUDA(cudaMalloc(&p, n));
         bytes = n;
+    }
+    // grow-only from the block cache; the block is used on stream st
+    void ensure_cached(size_t n, cudaStream_t st) {
+        if (n <= bytes && p && cached && cst == st) return;
+        release();
+        if (n == 0) n = 16;
+        p = devcache_get(n, st, &bytes);
+        cached = true;
+        cst = st;
     }
     // stream-ordered allocation / release (cudaMallocAsync pool)
     void alloc_async(size_t n, cudaStream_t st) {
@@ -162,9 +193,14 @@ struct DevBuf {
         bytes = n;
     }
     void release_async(cudaStream_t st) {
-        if (p) cudaFreeAsync(p, st);
+        if (p) {
+            if (cached) devcache_put(p, bytes, cst);
+            else cudaFreeAsync(p, st);
+        }
         p = nullptr;
         bytes = 0;
+        cst = nullptr;
+        cached = false;
     }
     template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };

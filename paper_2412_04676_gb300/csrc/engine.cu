@@ -31,6 +31,27 @@ double wall_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+void step_mark(Ctx& C, int phase) {
+    cudaEvent_t e = nullptr;
+    if (C.marks.size() < C.mark_pool.size()) {
+        e = C.mark_pool[C.marks.size()];
+    } else {
+        GBD_CHECK_CUDA(cudaEventCreate(&e));
+        C.mark_pool.push_back(e);
+    }
+    GBD_CHECK_CUDA(cudaEventRecord(e, C.cs));
+    C.marks.push_back({phase, e});
+}
+
+void step_marks_flush(Ctx& C) {
+    for (size_t i = 0; i + 1 < C.marks.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, C.marks[i].second, C.marks[i + 1].second) == cudaSuccess)
+            C.timers[C.marks[i].first] += ms;
+    }
+    C.marks.clear();
+}
+
 // ============================================================== bases
 EBasis left_enlarged(const Bond& b) {
     std::map<Q, std::vector<Seg>> m;
@@ -92,6 +113,13 @@ void make_classes(const std::vector<Q>& dq, OpSet& E) {
 void alloc_env(Ctx& C, OpSet& E) {
     E.layout();
     E.data.alloc_async(size_t(std::max<long long>(E.total, 2)) * sizeof(double), C.cs);
+    GBD_CHECK_CUDA(cudaMemsetAsync(E.data.p, 0, size_t(std::max<long long>(E.total, 2)) * sizeof(double), C.cs));
+}
+
+// enlarged operator sets live for one position only: from the block cache
+void alloc_env_cached(Ctx& C, OpSet& E) {
+    E.layout();
+    E.data.ensure_cached(size_t(std::max<long long>(E.total, 2)) * sizeof(double), C.cs);
     GBD_CHECK_CUDA(cudaMemsetAsync(E.data.p, 0, size_t(std::max<long long>(E.total, 2)) * sizeof(double), C.cs));
 }
 
@@ -239,7 +267,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             for (auto& s : mine) { s.blk = bidx; subs.push_back(std::move(s)); }
         }
     }
-    alloc_env(C, out);
+    alloc_env_cached(C, out);
     // upload coefficient matrices of the dense links
     std::vector<double> wall(size_t(std::max<long long>(wtot, 1)));
     for (size_t i = 0; i < links.size(); ++i)
@@ -521,13 +549,24 @@ void destroy_ctx(Ctx& C) {
         if (C.eig_st[i]) cudaStreamDestroy(C.eig_st[i]);
         C.eig_work[i].release();
     }
+    for (auto e : C.mark_pool) cudaEventDestroy(e);
+    C.mark_pool.clear();
+    C.marks.clear();
     if (C.ev0) cudaEventDestroy(C.ev0);
     if (C.ev1) cudaEventDestroy(C.ev1);
     C.envL.clear();
     C.envR.clear();
+    // every holder of a cached block (stream-ordered on C.cs) gives it back
+    // while C.cs still exists
     C.H = Heff();
+    C.sites.clear();
+    C.plan_a.free();
+    C.plan_b.free();
+    C.plan_c.free();
+    cudaDeviceSynchronize();
     if (C.cs) cudaStreamDestroy(C.cs);
     if (C.ios) cudaStreamDestroy(C.ios);
+    devcache_trim();
     C.cuda_ready = false;
 }
 
@@ -733,9 +772,9 @@ void setup_heff(Ctx& C, int b) {
     }
     H.dim = off;
     GBD_REQUIRE(H.dim > 0, GBD_ERR_STATE, "empty wavefunction space");
-    H.xin.ensure(size_t(H.dim) * sizeof(double));
-    H.yout.ensure(size_t(H.dim) * sizeof(double));
-    H.diag.ensure(size_t(H.dim) * sizeof(double));
+    H.xin.ensure_cached(size_t(H.dim) * sizeof(double), C.cs);
+    H.yout.ensure_cached(size_t(H.dim) * sizeof(double), C.cs);
+    H.diag.ensure_cached(size_t(H.dim) * sizeof(double), C.cs);
     // phase 1: X_{c,Q2}[t] = OL[t][Q,Q2] psi[Q2]; phase 2: Y[Q] += sum X[t] OR[t][Q,Q2]^T
     long long xtot = 0;
     H.op_bytes = double(H.OL.total + H.OR.total) * 8.0;
@@ -782,7 +821,7 @@ void setup_heff(Ctx& C, int b) {
 // position (mixed-precision runs may never need them).
 void build_fp64_plans(Ctx& C) {
     Heff& H = C.H;
-    H.X.ensure(size_t(std::max<long long>(H.xtot, 1)) * sizeof(double));
+    H.X.ensure_cached(size_t(std::max<long long>(H.xtot, 1)) * sizeof(double), C.cs);
     const double* dOL = H.OL.data.as<double>();
     const double* dOR = H.OR.data.as<double>();
     double* dX = H.X.as<double>();
@@ -1248,11 +1287,11 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         rtot += (long long)m[i] * m[i];
     }
     DevBuf rho, evals, info;
-    rho.ensure(size_t(std::max<long long>(rtot, 1)) * sizeof(double));
+    rho.ensure_cached(size_t(std::max<long long>(rtot, 1)) * sizeof(double), s);
     long long etot = 0;
     for (int i = 0; i < ns; ++i) etot += m[i];
-    evals.ensure(size_t(std::max<long long>(etot, 1)) * sizeof(double));
-    info.ensure(sizeof(int) * (ns + 1));
+    evals.ensure_cached(size_t(std::max<long long>(etot, 1)) * sizeof(double), s);
+    info.ensure_cached(sizeof(int) * (ns + 1), s);
     GemmPlan& P = C.plan_c;
     P.clear();
     for (int i = 0; i < ns; ++i) {
@@ -1272,6 +1311,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         else { g.lda = mR; g.ldb = mR; g.transA = 1; g.K = mL; }
         P.add_task(t, {g});
     }
+    if (!C.marks.empty()) step_mark(C, Ctx::T_PH_RHO_EIG);
     P.check({{C.psi.p, C.psi.bytes}, {rho.p, rho.bytes}}, "truncate/rho");
     P.upload(s);
     P.launch(s);
@@ -1370,7 +1410,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         itot += (long long)I.basis.dim[I.basis.find(nb.q[i])] * nb.dim[i];
     }
     I.total = itot;
-    I.data.ensure(size_t(std::max<long long>(itot, 1)) * sizeof(double));
+    I.data.ensure_cached(size_t(std::max<long long>(itot, 1)) * sizeof(double), s);
     // C = U^T psi (dir +1) or psi V (dir -1), per kept sector
     std::vector<long long> coff(nb.q.size());
     long long ctot = 0;
@@ -1381,7 +1421,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         ctot += (long long)nb.dim[i] * other;
     }
     DevBuf Cbuf;
-    Cbuf.ensure(size_t(std::max<long long>(ctot, 1)) * sizeof(double));
+    Cbuf.ensure_cached(size_t(std::max<long long>(ctot, 1)) * sizeof(double), s);
     P.clear();
     for (size_t i = 0; i < nb.q.size(); ++i) {
         int si = H.sector_of(nb.q[i]);
@@ -1414,8 +1454,10 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     P.launch(s);
     // renormalised environment of the truncated block (row a6)
     auto E = std::make_unique<OpSet>();
+    if (!C.marks.empty()) step_mark(C, Ctx::T_PH_RENORM);
     if (dir == 1) renormalize(C, H.OL, I, *E);
     else renormalize(C, H.OR, I, *E);
+    if (!C.marks.empty()) step_mark(C, Ctx::T_PH_NEXT);
     // next two-site vector ("StVec")
     const int L = C.L;
     if (dir == 1) {

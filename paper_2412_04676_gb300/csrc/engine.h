@@ -115,7 +115,11 @@ struct Ctx {
     enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2,
            T_PROD_MS0, T_PROD_MS1, T_PROD_MS2, T_PROD_N0, T_PROD_N1, T_PROD_N2, T_TC_ISSUE_SL,
            T_PREP_SPLIT, T_PREP_PLAN, T_PREP_UPLOAD, T_PROD_GF0, T_PROD_GF1, T_PROD_GF2,
-           T_REN_TC_GFLOP, T_ENL_TC_GFLOP, T_COUNT };
+           T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
+           // device time of the phases of gbd_step on the compute stream (host gaps included)
+           T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO, T_COUNT };
+    std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
+    std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};
 };
 
@@ -127,6 +131,8 @@ void finalize_sites(Ctx& C);
 void build_envs(Ctx& C, int b);
 void setup_heff(Ctx& C, int b);
 double wall_ms();  // host wall clock in ms
+void step_mark(Ctx& C, int phase);  // phase (a T_PH_* index) starts now on the compute stream
+void step_marks_flush(Ctx& C);      // after the stream is synchronised: accumulate the phase times
 void apply_heff_dev(Ctx& C, const double* in, double* out, int precision);
 void heff_diag(Ctx& C);
 int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);

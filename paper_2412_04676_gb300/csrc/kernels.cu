@@ -17,6 +17,9 @@
 #include "kernels.h"
 
 #include <atomic>
+#include <iterator>
+#include <map>
+#include <mutex>
 
 namespace gbd {
 
@@ -110,14 +113,13 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(const GemmTask* __restrict
 
 template <class T>
 void upload_vec(const std::vector<T>& v, void*& d, size_t& cap, cudaStream_t st) {
+    // grow-only device table from the block cache (the plan is launched on st)
     size_t bytes = v.size() * sizeof(T);
     if (bytes == 0) return;
     if (bytes > cap) {
-        if (d) cudaFree(d);
-        d = nullptr;
-        size_t nb = std::max(bytes, cap * 2);
-        GBD_CHECK_CUDA(cudaMalloc(&d, nb));
-        cap = nb;
+        const size_t nb = std::max(bytes, cap * 2);
+        if (d) devcache_put(d, cap, st);
+        d = devcache_get(nb, st, &cap);
     }
     GBD_CHECK_CUDA(cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, st));
 }
@@ -177,6 +179,8 @@ void GemmPlan::check(const std::vector<std::pair<const void*, size_t>>& bufs, co
 }
 
 void GemmPlan::upload(cudaStream_t st) {
+    if (st_last && st_last != st) free();  // the tables' users move to another stream
+    st_last = st;
     upload_vec(tasks, d_tasks, cap_tasks, st);
     upload_vec(segs, d_segs, cap_segs, st);
     upload_vec(tiles, d_tiles, cap_tiles, st);
@@ -194,9 +198,14 @@ void GemmPlan::launch(cudaStream_t st) const {
 }
 
 void GemmPlan::free() {
-    if (d_tasks) cudaFree(d_tasks);
-    if (d_segs) cudaFree(d_segs);
-    if (d_tiles) cudaFree(d_tiles);
+    auto rel = [&](void* d, size_t cap) {
+        if (!d) return;
+        if (st_last) devcache_put(d, cap, st_last);
+        else cudaFree(d);
+    };
+    rel(d_tasks, cap_tasks);
+    rel(d_segs, cap_segs);
+    rel(d_tiles, cap_tiles);
     d_tasks = d_segs = d_tiles = nullptr;
     cap_tasks = cap_segs = cap_tiles = 0;
 }
@@ -475,6 +484,97 @@ void unpack_launch(const unsigned char* base, const PackItem* d_items, const Pac
                    unsigned long long* d_cks, cudaStream_t st) {
     if (n_chunks > 0) { unpack_payload_kernel<<<n_chunks, PT, 0, st>>>(base, d_items, d_chunks, d_cks); count_launch(); }
     GBD_CHECK_CUDA(cudaGetLastError());
+}
+
+// ============================================================== device block cache
+namespace {
+struct CacheBlock {
+    void* p;
+    size_t bytes;
+    cudaEvent_t ev;
+    int dev;
+};
+std::mutex g_cache_mu;
+std::multimap<size_t, CacheBlock> g_cache;
+size_t g_cache_bytes = 0;
+constexpr size_t kCacheMax = size_t(96) << 30;  // cached bytes kept at most
+}  // namespace
+
+void* devcache_get(size_t n, cudaStream_t st, size_t* got) {
+    int dev = 0;
+    GBD_CHECK_CUDA(cudaGetDevice(&dev));
+    {
+        std::unique_lock<std::mutex> lk(g_cache_mu);
+        // best fit within 1.5x of the request, on this device
+        for (auto it = g_cache.lower_bound(n); it != g_cache.end() && it->first <= n + n / 2 + (size_t(1) << 20); ++it) {
+            if (it->second.dev != dev) continue;
+            CacheBlock b = it->second;
+            g_cache.erase(it);
+            g_cache_bytes -= b.bytes;
+            lk.unlock();
+            GBD_CHECK_CUDA(cudaStreamWaitEvent(st, b.ev, 0));
+            cudaEventDestroy(b.ev);
+            *got = b.bytes;
+            return b.p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+        cudaGetLastError();
+        devcache_trim();
+        GBD_CHECK_CUDA(cudaMalloc(&p, n));
+    }
+    *got = n;
+    return p;
+}
+
+void devcache_put(void* p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    int dev = 0;
+    cudaEvent_t ev = nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, st) != cudaSuccess) {
+        if (ev) cudaEventDestroy(ev);
+        cudaGetLastError();
+        cudaFree(p);  // synchronises: safe without the event
+        return;
+    }
+    std::vector<CacheBlock> evict;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_cache.insert({bytes, {p, bytes, ev, dev}});
+        g_cache_bytes += bytes;
+        while (g_cache_bytes > kCacheMax && !g_cache.empty()) {
+            auto it = std::prev(g_cache.end());  // the largest
+            evict.push_back(it->second);
+            g_cache_bytes -= it->second.bytes;
+            g_cache.erase(it);
+        }
+    }
+    for (auto& b : evict) {
+        cudaEventSynchronize(b.ev);
+        cudaEventDestroy(b.ev);
+        cudaFree(b.p);
+    }
+}
+
+void devcache_trim() {
+    std::vector<CacheBlock> all;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (auto& kv : g_cache) all.push_back(kv.second);
+        g_cache.clear();
+        g_cache_bytes = 0;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& b : all) {
+        cudaSetDevice(b.dev);
+        cudaEventSynchronize(b.ev);
+        cudaEventDestroy(b.ev);
+        cudaFree(b.p);
+    }
+    cudaSetDevice(cur);
 }
 
 }  // namespace gbd

@@ -46,6 +46,7 @@ struct GemmPlan {
     void* d_segs = nullptr;
     void* d_tiles = nullptr;
     size_t cap_tasks = 0, cap_segs = 0, cap_tiles = 0;
+    cudaStream_t st_last = nullptr;  // stream of the last upload (the tables' users)
     double flops = 0.0;  // 2*M*N*K summed (useful)
     void clear() { tasks.clear(); segs.clear(); tiles.clear(); flops = 0.0; }
     void add_task(GemmTask t, const std::vector<GemmSeg>& s);
@@ -55,7 +56,29 @@ struct GemmPlan {
     // writes lies inside one of the given buffers (base, bytes).
     void check(const std::vector<std::pair<const void*, size_t>>& bufs, const char* what) const;
     void free();
+    GemmPlan() = default;
+    GemmPlan(const GemmPlan&) = delete;
+    GemmPlan& operator=(const GemmPlan&) = delete;
+    GemmPlan(GemmPlan&& o) noexcept { take(o); }
+    GemmPlan& operator=(GemmPlan&& o) noexcept {
+        if (this != &o) { free(); take(o); }
+        return *this;
+    }
     ~GemmPlan() { free(); }
+
+  private:
+    void take(GemmPlan& o) {
+        tasks = std::move(o.tasks);
+        segs = std::move(o.segs);
+        tiles = std::move(o.tiles);
+        d_tasks = o.d_tasks; d_segs = o.d_segs; d_tiles = o.d_tiles;
+        cap_tasks = o.cap_tasks; cap_segs = o.cap_segs; cap_tiles = o.cap_tiles;
+        st_last = o.st_last;
+        flops = o.flops;
+        o.d_tasks = o.d_segs = o.d_tiles = nullptr;
+        o.cap_tasks = o.cap_segs = o.cap_tiles = 0;
+        o.st_last = nullptr;
+    }
 };
 
 // ------------------------------------------------------------------ vectors

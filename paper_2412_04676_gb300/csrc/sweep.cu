@@ -448,9 +448,12 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     GBD_CHECK_CUDA(cudaEventCreate(&ea));
     GBD_CHECK_CUDA(cudaEventCreate(&eb));
     GBD_CHECK_CUDA(cudaEventRecord(ea, C.cs));
+    C.marks.clear();
+    step_mark(C, Ctx::T_PH_RESIDENT);
     // pre-processing: environments resident, enlarged operators
     ensure_resident(C, 0, b);
     ensure_resident(C, 1, b + 2);
+    step_mark(C, Ctx::T_PH_ENLARGE);
     if (C.H.b != b || !C.H.OL.resident()) setup_heff(C, b);
     if (off) {  // both environments are consumed by the enlargement
         release_async(C, 0, b);
@@ -459,10 +462,12 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     double t1 = now_ms();
     double e = 0.0;
     gbd_dav_stats ds{};
+    step_mark(C, Ctx::T_PH_DAVIDSON);
     davidson(C, nullptr, &e, &ds);
     double flops = C.H.flops * ds.matvecs;
     double t2 = now_ms();
     double w = truncate_step(C, dir, D);
+    step_mark(C, Ctx::T_PH_IO);
     if (off) {
         // Sec. III.B.4: the next environment is loaded right after the
         // renormalisation, then the new one is saved asynchronously
@@ -476,8 +481,10 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
         if (dir == 1) save_async(C, 0, b + 1);
         else save_async(C, 1, b + 1);
     }
+    step_mark(C, Ctx::T_PH_IO);  // closing mark
     GBD_CHECK_CUDA(cudaEventRecord(eb, C.cs));
     GBD_CHECK_CUDA(cudaEventSynchronize(eb));
+    step_marks_flush(C);
     float msd = 0.f;
     cudaEventElapsedTime(&msd, ea, eb);
     cudaEventDestroy(ea);

@@ -756,7 +756,7 @@ long long op_layout(const OpSet& O, std::vector<std::vector<long long>>& off) {
 }
 
 template <class T> void upload_vec(DevBuf& d, const std::vector<T>& v, cudaStream_t st) {
-    d.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+    d.ensure_cached(std::max<size_t>(v.size() * sizeof(T), 16), st);
     if (!v.empty()) GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
 }
 
@@ -858,8 +858,8 @@ template <int MODE> void build_plan(Ctx& C) {
     std::vector<std::vector<long long>> offL, offR;
     P.nL = std::max(op_layout(H.OL, offL), 8LL);
     P.nR = std::max(op_layout(H.OR, offR), 8LL);
-    P.ol.ensure(size_t(P.nL) * NS * 2);
-    P.orr.ensure(size_t(P.nR) * NS * 2);
+    P.ol.ensure_cached(size_t(P.nL) * NS * 2, st);
+    P.orr.ensure_cached(size_t(P.nR) * NS * 2, st);
     P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
     {
         DevBuf d;
@@ -901,7 +901,7 @@ template <int MODE> void build_plan(Ctx& C) {
     // ---- psi^T slice planes
     P.np = 8;
     for (const auto& ps : T.psec) P.np = std::max(P.np, ps.dst + (long long)ps.mR * ps.ldp);
-    P.psi.ensure(size_t(P.np) * NS * 2);
+    P.psi.ensure_cached(size_t(P.np) * NS * 2, st);
     {
         // psi^T per sector: row n of the operand is column n of psi
         std::vector<SplitDesc> sd;
@@ -935,7 +935,7 @@ template <int MODE> void build_plan(Ctx& C) {
         }
     }
     P.nx = std::max(nx, 8LL);
-    P.x.ensure(size_t(P.nx) * NS * 2);
+    P.x.ensure_cached(size_t(P.nx) * NS * 2, st);
     // ---- tensor maps: one per operand, the NS slice planes as outer dimension
     std::vector<CUtensorMap> maps;
     auto add_maps = [&](const __nv_bfloat16* base, long long plane, int K, long long rows, int layers, int ld,
@@ -1056,7 +1056,7 @@ template <int MODE> void build_plan(Ctx& C) {
                 red.push_back(r);
             }
     }
-    P.partial.ensure(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2));
+    P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
     for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
     // tensor-core work issued per product (whole 128-row tiles at the MMA
     // width, every slice product): the gap to the useful flops is padding
@@ -1115,7 +1115,7 @@ void tc_prepare(Ctx& C, int mode) {
             T.psec.push_back({H.soff[s], np, mL, mR, pad8(mL)});
             np += (long long)mR * pad8(mL);
         }
-        T.err.ensure(sizeof(int));
+        T.err.ensure_cached(sizeof(int), st);
         GBD_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
         int dev = 0;
         GBD_CHECK_CUDA(cudaGetDevice(&dev));
@@ -1204,7 +1204,7 @@ bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, c
         nu += (long long)U.out.dim[q] * pad8(U.basis.dim[e]);
     }
     nu = std::max(nu, 8LL);
-    T.ren_u.ensure(size_t(nu) * NS * 2);
+    T.ren_u.ensure_cached(size_t(nu) * NS * 2, st);
     std::vector<SplitDesc> sd;
     for (size_t q = 0; q < U.out.q.size(); ++q) {
         if (uoff[q] < 0) continue;
