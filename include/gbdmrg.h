@@ -336,8 +336,9 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * sliced form (the FP64 GFLOP counters above count FP64 GEMMs only), then
  * the device time (ms, compute stream, host gaps included) of the phases of
  * gbd_step: environments resident, enlargement, Davidson, density matrices
- * and eigensolves, renormalisation, next start vector, IO scheduling.  *n
- * gets the count; out may be NULL. */
+ * and eigensolves, renormalisation, next start vector, IO scheduling, then
+ * the enlargement planning (host) in three parts: coefficient links, output
+ * blocks, copy and GEMM items.  *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

@@ -228,6 +228,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             for (const auto& x : ents[i]) links[i].W[size_t(std::get<0>(x)) * Tout + std::get<1>(x)] += std::get<2>(x);
         }
     }
+    const double t_links = wall_ms();
     std::map<std::tuple<int, int, int>, std::vector<int>> by_cst;  // (co, s, t) -> links
     long long wtot = 0;
     for (size_t i = 0; i < links.size(); ++i) {
@@ -267,6 +268,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             for (auto& s : mine) { s.blk = bidx; subs.push_back(std::move(s)); }
         }
     }
+    const double t_subs = wall_ms();
     alloc_env_cached(C, out);
     // upload coefficient matrices of the dense links
     std::vector<double> wall(size_t(std::max<long long>(wtot, 1)));
@@ -280,7 +282,20 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     GemmPlan& P = C.plan_a;
     P.clear();
     std::vector<CopyItem> items;
-    std::vector<CopySrc> srcs;
+    std::vector<CopyLink> clinks;
+    std::vector<CopyCol> ccols;
+    std::vector<CopyCoef> ccoefs;
+    // per sparse link, its (input layer, coefficient) lists per output layer
+    std::vector<int> link_col0(links.size(), -1);
+    for (size_t i = 0; i < links.size(); ++i) {
+        if (!sparse[i]) continue;
+        link_col0[i] = int(ccols.size());
+        for (const auto& v : col_src[i]) {
+            ccols.push_back({int(ccoefs.size()), int(v.size())});
+            for (const auto& av : v) ccoefs.push_back({av.first, av.second});
+        }
+    }
+    int max_tout = 0;
     // mixed form: the dense coefficient GEMMs run on the tensor cores in the
     // sliced form (FP64 GEMMs otherwise)
     const bool tc_env = C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2;
@@ -333,34 +348,44 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
             tc_tasks.push_back({dsub, t.ldc, t.ldr, t.M, t.N, t.ncols, tc_seg0, int(tc_segs.size()) - tc_seg0});
         if (!segs.empty()) P.add_task(t, segs);
         if (sp.empty()) continue;
-        for (int c = 0; c < Tout; ++c) {
-            const int src0 = int(srcs.size());
-            for (const auto& lb : sp)
-                for (const auto& av : col_src[lb.first][c])
-                    srcs.push_back({din + lb.second->off + (long long)av.first * lb.second->rows * lb.second->cols, av.second});
-            const int nsrc = int(srcs.size()) - src0;
-            if (nsrc == 0) continue;
-            CopyItem it{};
-            it.dst = dsub + (long long)c * ob.rows * ob.cols;
-            it.ldr = ob.cols;
-            it.rows = sub.rows;
-            it.cols = sub.cols;
-            it.src0 = src0;
-            it.nsrc = nsrc;
-            items.push_back(it);
-        }
+        CopyItem it{};
+        it.dst = dsub;
+        it.out_pitch = (long long)ob.rows * ob.cols;
+        it.ldr = ob.cols;
+        it.rows = sub.rows;
+        it.cols = sub.cols;
+        it.tout = Tout;
+        it.link0 = int(clinks.size());
+        for (const auto& lb : sp)
+            clinks.push_back({din + lb.second->off, (long long)lb.second->rows * lb.second->cols, link_col0[lb.first]});
+        it.nlink = int(clinks.size()) - it.link0;
+        items.push_back(it);
+        max_tout = std::max(max_tout, Tout);
     }
     P.check({{C.scratch_w.p, C.scratch_w.bytes}, {Ein.data.p, size_t(Ein.total) * 8}, {out.data.p, size_t(out.total) * 8}},
             "enlarge");
-    // host-side bounds check of the copies
+    const double t_items = wall_ms();
+    // host-side bounds check of the copies: outputs inside their block arena,
+    // inputs inside the environment
     for (const auto& it : items) {
-        const char* lo = reinterpret_cast<const char*>(out.data.p);
-        const char* a = reinterpret_cast<const char*>(it.dst);
-        const char* e = reinterpret_cast<const char*>(it.dst + (long long)(it.rows - 1) * it.ldr + it.cols);
-        GBD_REQUIRE(a >= lo && e <= lo + size_t(out.total) * 8, GBD_ERR_STATE, "enlarge: copy outside its block");
+        const double* e = it.dst + (long long)(it.tout - 1) * it.out_pitch + (long long)(it.rows - 1) * it.ldr + it.cols;
+        GBD_REQUIRE(it.dst >= dout && e <= dout + out.total, GBD_ERR_STATE, "enlarge: copy outside its block");
+        for (int l = it.link0; l < it.link0 + it.nlink; ++l) {
+            const CopyLink& L = clinks[l];
+            const CopyCol* cc = ccols.data() + L.col0;
+            for (int c = 0; c < it.tout; ++c)
+                for (int k = cc[c].c0; k < cc[c].c0 + cc[c].n; ++k) {
+                    const double* a = L.src + (long long)ccoefs[k].a * L.in_pitch;
+                    GBD_REQUIRE(a >= din && a + (long long)it.rows * it.cols <= din + Ein.total, GBD_ERR_STATE,
+                                "enlarge: copy source outside the environment");
+                }
+        }
     }
     const double t_dev0 = wall_ms();
     C.timers[Ctx::T_ENL_HOST] += t_dev0 - t_host0;
+    C.timers[Ctx::T_ENL_H_LINKS] += t_links - t_host0;
+    C.timers[Ctx::T_ENL_H_SUBS] += t_subs - t_links;
+    C.timers[Ctx::T_ENL_H_ITEMS] += t_items - t_subs;
     C.timers[Ctx::T_ENL_GFLOP] += P.flops * 1e-9;
     P.upload(C.cs);
     P.launch(C.cs);
@@ -378,13 +403,16 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         C.timers[Ctx::T_ENL_TC_GFLOP] += tc_flops * 1e-9;
     }
     if (!items.empty()) {
-        C.scratch_items.ensure(items.size() * sizeof(CopyItem));
-        C.scratch_srcs.ensure(std::max<size_t>(srcs.size(), 1) * sizeof(CopySrc));
-        GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_items.p, items.data(), items.size() * sizeof(CopyItem),
-                                       cudaMemcpyHostToDevice, C.cs));
-        GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_srcs.p, srcs.data(), srcs.size() * sizeof(CopySrc), cudaMemcpyHostToDevice,
-                                       C.cs));
-        copy_sum(C.scratch_items.as<CopyItem>(), int(items.size()), C.scratch_srcs.as<CopySrc>(), C.cs);
+        auto up = [&](DevBuf& d, const void* src, size_t bytes) {  // context buffers, grow-only
+            d.ensure(std::max<size_t>(bytes, 16));
+            if (bytes) GBD_CHECK_CUDA(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, C.cs));
+        };
+        up(C.scratch_items, items.data(), items.size() * sizeof(CopyItem));
+        up(C.scratch_srcs, clinks.data(), clinks.size() * sizeof(CopyLink));
+        up(C.scratch_cols, ccols.data(), ccols.size() * sizeof(CopyCol));
+        up(C.scratch_coefs, ccoefs.data(), ccoefs.size() * sizeof(CopyCoef));
+        copy_sum(C.scratch_items.as<CopyItem>(), int(items.size()), max_tout, C.scratch_srcs.as<CopyLink>(),
+                 C.scratch_cols.as<CopyCol>(), C.scratch_coefs.as<CopyCoef>(), C.cs);
     }
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
     C.timers[Ctx::T_ENL_DEV] += wall_ms() - t_dev0;

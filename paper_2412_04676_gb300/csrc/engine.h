@@ -98,7 +98,7 @@ struct Ctx {
     int psi_b = -1;
     // scratch
     GemmPlan plan_a, plan_b, plan_c;
-    DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small, scratch_items, scratch_srcs;
+    DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small, scratch_items, scratch_srcs, scratch_cols, scratch_coefs;
     DevBuf env_sl_w, env_sl_e, env_err;  // sliced operands of the tensor-core enlargement
     DevBuf dav_V, dav_AV, dav_r, dav_t, dav_x, dav_ax, dav_tmp;
     DevBuf stage;  // device staging for pack/unpack through pageable memory
@@ -117,7 +117,8 @@ struct Ctx {
            T_PREP_SPLIT, T_PREP_PLAN, T_PREP_UPLOAD, T_PROD_GF0, T_PROD_GF1, T_PROD_GF2,
            T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
            // device time of the phases of gbd_step on the compute stream (host gaps included)
-           T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO, T_COUNT };
+           T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
+           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};

@@ -338,22 +338,40 @@ void fill_zero(double* p, long long n, cudaStream_t st) {
 
 // ============================================================== scaled copies
 namespace {
-__global__ void copy_sum_kernel(const CopyItem* __restrict__ items, const CopySrc* __restrict__ srcs) {
+__global__ void copy_sum_kernel(const CopyItem* __restrict__ items, const CopyLink* __restrict__ links,
+                                const CopyCol* __restrict__ cols, const CopyCoef* __restrict__ coefs) {
     const CopyItem it = items[blockIdx.x];
     const int n = it.rows * it.cols;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        double v = 0.0;
-        for (int k = it.src0; k < it.src0 + it.nsrc; ++k) v = fma(srcs[k].coef, srcs[k].src[e], v);
-        const int r = e / it.cols, c = e % it.cols;
-        it.dst[(long long)r * it.ldr + c] += v;
+    const int c_end = min(it.tout, int(blockIdx.y + 1) * kCopyLayers);
+    for (int c = blockIdx.y * kCopyLayers; c < c_end; ++c) {
+        double* dst = it.dst + (long long)c * it.out_pitch;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            double v = 0.0;
+            bool any = false;
+            for (int l = it.link0; l < it.link0 + it.nlink; ++l) {
+                const CopyLink L = links[l];
+                const CopyCol col = cols[L.col0 + c];
+                for (int k = col.c0; k < col.c0 + col.n; ++k) {
+                    v = fma(coefs[k].coef, L.src[(long long)coefs[k].a * L.in_pitch + e], v);
+                    any = true;
+                }
+            }
+            if (!any) continue;
+            const int r = e / it.cols, cc = e - r * it.cols;
+            dst[(long long)r * it.ldr + cc] += v;
+        }
     }
 }
 }  // namespace
 
-void copy_sum(const CopyItem* d_items, int n_items, const CopySrc* d_srcs, cudaStream_t st) {
+void copy_sum(const CopyItem* d_items, int n_items, int max_tout, const CopyLink* d_links, const CopyCol* d_cols,
+              const CopyCoef* d_coefs, cudaStream_t st) {
+    if (n_items <= 0 || max_tout <= 0) return;
+    const unsigned gy = unsigned((max_tout + kCopyLayers - 1) / kCopyLayers);
+    GBD_REQUIRE(gy <= 65535, GBD_ERR_ARG, "copy_sum: too many output layers");
     for (int i0 = 0; i0 < n_items; i0 += 0x7FFFFFF) {
         int n = std::min(n_items - i0, 0x7FFFFFF);
-        copy_sum_kernel<<<n, 128, 0, st>>>(d_items + i0, d_srcs);
+        copy_sum_kernel<<<dim3(n, gy), 128, 0, st>>>(d_items + i0, d_links, d_cols, d_coefs);
         count_launch();
     }
     GBD_CHECK_CUDA(cudaGetLastError());

@@ -131,17 +131,35 @@ void unpack_launch(const unsigned char* stream_base, const PackItem* d_items, co
                    int n_chunks, unsigned long long* d_cks, cudaStream_t st);
 
 // ------------------------------------------------------------------ scaled copies
-// dst (rows x cols, row stride ldr) += sum_k coef_k * src_k (contiguous rows x cols)
-struct CopySrc {
-    const double* src;
+// Enlargement pass-through links (Sec. II.B step 1): output layer c of a
+// sub-block (rows x cols, row stride ldr, layer stride out_pitch) +=
+// sum over the sub-block's links l of sum_(a, coef) in cols(l, c) of
+// coef * input layer a of l's input block (contiguous rows x cols, layer
+// stride in_pitch).  cols(l, c) depends on the link only, so it is stored
+// once per link and shared by every sub-block the link feeds.
+struct CopyCoef {
+    int a;           // input layer
     double coef;
 };
-struct CopyItem {
-    double* dst;
-    long long ldr;
-    int rows, cols, src0, nsrc;
+struct CopyCol {
+    int c0, n;       // CopyCoef range of one (link, output layer)
 };
-void copy_sum(const CopyItem* d_items, int n_items, const CopySrc* d_srcs, cudaStream_t st);
+struct CopyLink {
+    const double* src;   // input block, layer 0
+    long long in_pitch;  // elements between input layers
+    int col0;            // CopyCol index of output layer 0 of this link
+};
+struct CopyItem {
+    double* dst;          // output sub-block, layer 0
+    long long out_pitch;  // elements between output layers
+    long long ldr;
+    int rows, cols, tout; // sub-block shape, output layers
+    int link0, nlink;     // CopyLink range
+};
+// grid: (items, ceil(max tout / kCopyLayers)); each (item, layer) has one writer
+constexpr int kCopyLayers = 8;
+void copy_sum(const CopyItem* d_items, int n_items, int max_tout, const CopyLink* d_links, const CopyCol* d_cols,
+              const CopyCoef* d_coefs, cudaStream_t st);
 
 // ------------------------------------------------------------------ misc
 // Count of this library's kernel launches (incremented by every launcher).

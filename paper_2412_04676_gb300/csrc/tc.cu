@@ -590,15 +590,15 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
     const int nb64 = (b.ldd + 63) >> 6;
     const int G = b.ldd > 16 ? 32 : (b.ldd > 8 ? 16 : 8);
     const int upw = 32 / G;  // units per warp and iteration
-    const long long units = b.rows * nb64;
+    const int units = int(b.rows) * nb64;  // a descriptor covers at most max(kSplitUnits, nb64) units
     const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-    const long long nw = blockDim.x >> 5;
+    const int nw = blockDim.x >> 5;
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.src);
-    for (long long u0 = (threadIdx.x >> 5) * upw; u0 < units; u0 += nw * upw) {
-        const long long u = u0 + sub;
+    for (int u0 = (threadIdx.x >> 5) * upw; u0 < units; u0 += nw * upw) {
+        const int u = u0 + sub;
         const bool uv = u < units;
-        const long long r = uv ? u / nb64 : 0;
-        const int c0 = uv ? int(u - r * nb64) * 64 : 0;
+        const int r = uv ? u / nb64 : 0;
+        const int c0 = uv ? (u - r * nb64) * 64 : 0;
         unsigned long long bits[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -606,7 +606,12 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
             bits[h] = (uv && c < b.cols && c < c0 + 64) ? src[r * b.rs + (long long)c * b.cs] : 0ULL;
         }
         const long long ra = b.rbase + r;
-        __nv_bfloat16* d = b.dst + (ra / b.R) * b.lpitch + (ra % b.R) * b.rpitch;
+        long long doff = ra * b.rpitch;
+        if (b.lpitch != 0) {  // regrouped rows (block rows < 2^31)
+            const int t = int(ra) / int(b.R);
+            doff = (long long)t * b.lpitch + (ra - (long long)t * b.R) * b.rpitch;
+        }
+        __nv_bfloat16* d = b.dst + doff;
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
