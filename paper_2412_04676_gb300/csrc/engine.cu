@@ -517,19 +517,17 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
     PB.check(bufs, "renormalise/B");
     const double t_dev0 = wall_ms();
     C.timers[Ctx::T_REN_HOST] += t_dev0 - t_host0;
-    // mixed form: phase A (about dim/k of the flops) on the tensor cores in the
-    // sliced form when the enlarged set's slices exist; phase B stays FP64
-    if (C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2 &&
-        tc_renorm_phase_a(C, O, U, out, toff, tmp)) {
-        C.timers[Ctx::T_REN_TC_GFLOP] += PA.flops * 1e-9;
+    // mixed form: both GEMM phases on the tensor cores in the sliced form when
+    // the enlarged set's slices exist (FP64 GEMMs otherwise)
+    if (C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2 && tc_renormalize(C, O, U, out, toff, tmp)) {
+        C.timers[Ctx::T_REN_TC_GFLOP] += (PA.flops + PB.flops) * 1e-9;
     } else {
-        C.timers[Ctx::T_REN_GFLOP] += PA.flops * 1e-9;
+        C.timers[Ctx::T_REN_GFLOP] += (PA.flops + PB.flops) * 1e-9;
         PA.upload(C.cs);
         PA.launch(C.cs);
+        PB.upload(C.cs);
+        PB.launch(C.cs);
     }
-    C.timers[Ctx::T_REN_GFLOP] += PB.flops * 1e-9;
-    PB.upload(C.cs);
-    PB.launch(C.cs);
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
     C.timers[Ctx::T_REN_DEV] += wall_ms() - t_dev0;
 }

@@ -1179,14 +1179,17 @@ void tc_apply(Ctx& C, int mode) {
     if (mode == 0) run_plan<0>(C); else run_plan<1>(C);
 }
 
-// Phase A of the renormalisation (Sec. II.B step 3) on the tensor cores in the
-// sliced form: tmp (T*dimO x k_i) = O_stacked (T*dimO x dimI) U_i for every
-// kept block, with O read from the sliced planes of the current enlarged set
-// (built for the anchor products) and U_i^T sliced here.  tmp[j] starts at
-// tmp + toff[j] for the j-th block of out in class order.  Returns false
-// (nothing launched) when the sliced planes of O are not built.
-bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, const std::vector<long long>& toff,
-                       double* tmp) {
+// The renormalisation (Sec. II.B step 3) on the tensor cores in the sliced
+// form, for every kept block j of out (class order):
+//   phase A: tmp_j (T*dimO x k_i) = O_stacked (T*dimO x dimI) U_i, O read from
+//            the sliced planes of the current enlarged set (built for the
+//            anchor products), U^T sliced here; tmp_j at tmp + toff[j] (FP64);
+//   phase B: new_j[t] (k_o x k_i) = U_o^T tmp_j[t] for all layers t at once as
+//            U_o^T [tmp_j[0] | tmp_j[1] | ...], with tmp_j transposed and
+//            sliced per layer, written into out's arena.
+// Returns false (nothing launched) when the sliced planes of O are not built.
+bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std::vector<long long>& toff,
+                    double* tmp) {
     Heff& H = C.H;
     TcHeff& T = H.tc;
     if (!H.tc_ready || !T.pl[1].built) return false;
@@ -1267,7 +1270,6 @@ bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, c
             ++j;
         }
     }
-    if (works.empty()) return true;
     auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
     std::stable_sort(works.begin(), works.end(), longer);
     DevBuf dmaps, dsegs, dworks;
@@ -1277,9 +1279,88 @@ bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, c
     GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         KT<1, 3>::SMEM_BYTES));
     const int nw = int(works.size());
-    tc_gemm_kernel<1, 3><<<std::min(nw, T.n_sm), THREADS, KT<1, 3>::SMEM_BYTES, st>>>(
-        dworks.as<Work>(), nw, dsegs.as<KSeg>(), dmaps.as<CUtensorMap>(), T.err.as<int>());
-    count_launch();
+    if (nw > 0) {
+        tc_gemm_kernel<1, 3><<<std::min(nw, T.n_sm), THREADS, KT<1, 3>::SMEM_BYTES, st>>>(
+            dworks.as<Work>(), nw, dsegs.as<KSeg>(), dmaps.as<CUtensorMap>(), T.err.as<int>());
+        count_launch();
+    }
+    GBD_CHECK_CUDA(cudaGetLastError());
+    // ---- phase B: tmp_j^T per layer, sliced: rows (t, k_i), K = dimO
+    std::vector<long long> toffT;
+    long long nt = 0;
+    for (size_t c = 0; c < out.cls.size(); ++c) {
+        const int Tn = int(out.cls[c].states.size());
+        for (const auto& nb : out.cls[c].blocks) {
+            const int dimO = U.basis.dim[U.basis.find(nb.Qo)];
+            toffT.push_back(nt);
+            nt += (long long)Tn * nb.cols * pad8(dimO);
+        }
+    }
+    nt = std::max(nt, 8LL);
+    T.ren_t.ensure_cached(size_t(nt) * NS * 2, st);
+    std::vector<SplitDesc> sdB;
+    std::vector<CUtensorMap> mapsB;
+    std::vector<KSeg> segsB;
+    std::vector<Work> worksB;
+    j = 0;
+    double* dN = out.data.as<double>();
+    for (size_t c = 0; c < out.cls.size(); ++c) {
+        const int Tn = int(out.cls[c].states.size());
+        for (const auto& nb : out.cls[c].blocks) {
+            const int dimO = U.basis.dim[U.basis.find(nb.Qo)];
+            const int ki = nb.cols, ko = nb.rows;
+            // element (row kk, col r) of tmp_j[t]^T is tmp_j[(t*dimO + r)*ki + kk]
+            const long long per = std::max<long long>(1, kSplitUnits / ((pad8(dimO) + 63) / 64));
+            for (int t = 0; t < Tn; ++t)
+                for (long long r0 = 0; r0 < ki; r0 += per)
+                    sdB.push_back({tmp + toff[j] + (long long)t * dimO * ki + r0, 1, ki, std::min<long long>(per, ki - r0),
+                                   dimO, pad8(dimO), T.ren_t.as<__nv_bfloat16>() + toffT[j] + (long long)t * ki * pad8(dimO),
+                                   nt, 1LL << 62, 0, pad8(dimO), r0});
+            const int mA = int(mapsB.size());
+            mapsB.push_back(make_map(T.ren_u.as<__nv_bfloat16>() + uoff[nb.qo], dimO, ko, 0, pad8(dimO), 0, NS, nu, BM));
+            mapsB.push_back(make_map(T.ren_t.as<__nv_bfloat16>() + toffT[j], dimO, (long long)Tn * ki, 0, pad8(dimO), 0, NS,
+                                     nt, TBN));
+            const int sidx = int(segsB.size());
+            segsB.push_back({mA, mA + 1, 0, 0, dimO, 1, 2, (dimO + BK - 1) / BK});
+            for (int m0 = 0; m0 < ko; m0 += BM)
+                for (long long n0 = 0; n0 < (long long)Tn * ki; n0 += TBN) {
+                    Work w{};
+                    w.m0 = m0;
+                    w.n0 = int(n0);
+                    w.M = ko;
+                    w.N = Tn * ki;
+                    w.seg0 = sidx;
+                    w.nseg = 1;
+                    w.c0 = 0;
+                    w.c1 = segsB[sidx].nchunk;
+                    w.out_kind = 2;
+                    w.promote = 1;
+                    w.ldo = ki;           // row pitch inside a layer
+                    w.ncols = ki;         // column t*ki + kk -> layer t, column kk
+                    w.ldr = (long long)ko * ki;
+                    w.out = dN + nb.off;
+                    worksB.push_back(w);
+                }
+            ++j;
+        }
+    }
+    DevBuf dsdB, dmapsB, dsegsB, dworksB;
+    upload_vec(dsdB, sdB, st);
+    for (size_t i0 = 0; i0 < sdB.size(); i0 += (1u << 30)) {
+        const unsigned n = unsigned(std::min<size_t>(1u << 30, sdB.size() - i0));
+        split_kernel<1><<<n, 256, 0, st>>>(dsdB.as<SplitDesc>() + i0);
+        count_launch();
+    }
+    if (!worksB.empty()) {
+        std::stable_sort(worksB.begin(), worksB.end(), longer);
+        upload_vec(dmapsB, mapsB, st);
+        upload_vec(dsegsB, segsB, st);
+        upload_vec(dworksB, worksB, st);
+        const int nwB = int(worksB.size());
+        tc_gemm_kernel<1, 3><<<std::min(nwB, T.n_sm), THREADS, KT<1, 3>::SMEM_BYTES, st>>>(
+            dworksB.as<Work>(), nwB, dsegsB.as<KSeg>(), dmapsB.as<CUtensorMap>(), T.err.as<int>());
+        count_launch();
+    }
     GBD_CHECK_CUDA(cudaGetLastError());
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the tables above are freed on return
     const int e = tc_error(C);

@@ -101,7 +101,7 @@ struct TcHeff {
     std::vector<PsiSec> psec;
     DevBuf err;                             // device error word
     int n_sm = 152;
-    DevBuf ren_u;                           // sliced U^T of the renormalisation
+    DevBuf ren_u, ren_t;                    // sliced U^T and tmp^T of the renormalisation
     GemmPlan blk_a, blk_b;                  // FP64 block-Hamiltonian terms (mode 0, optional)
     DevBuf blk_x;
     bool blk = false;
@@ -120,8 +120,7 @@ struct TcEnlTask { double* C; long long ldc, ldr; int M, N, ncols; int seg0, nse
 void tc_prepare(Ctx& C, int mode);
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
-bool tc_renorm_phase_a(Ctx& C, const OpSet& O, const Iso& U, const OpSet& out, const std::vector<long long>& toff,
-                       double* tmp);
+bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std::vector<long long>& toff, double* tmp);
 void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::vector<TcEnlSeg>& segs);
 
 }  // namespace gbd
