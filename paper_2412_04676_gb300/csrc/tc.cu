@@ -921,24 +921,19 @@ template <int MODE> void build_plan(Ctx& C) {
         P.n_psi = int(sd.size());
     }
     // ---- pairs (class, block) with their phase-1 outputs X
+    // (the position's (class, left block, right block) pairs, longest phase-1
+    // K first so the phase-1 work list comes out longest first)
     struct Pair { int c, bl, br, so, si; long long x; };
     std::vector<Pair> pairs;
+    pairs.reserve(H.pairs.size());
     long long nx = 0;
-    for (size_t c = 0; c < H.OL.cls.size(); ++c) {
-        const OpClass& cl = H.OL.cls[c];
-        const OpClass& cr = H.OR.cls[c];
-        for (size_t bi = 0; bi < cl.blocks.size(); ++bi) {
-            const OpBlock& ob = cl.blocks[bi];
-            int so = H.sector_of(ob.Qo), si = H.sector_of(ob.Qi);
-            if (so < 0 || si < 0) continue;
-            int br = -1;
-            for (size_t x = 0; x < cr.blocks.size(); ++x)
-                if (cr.blocks[x].Qo == ob.Qo && cr.blocks[x].Qi == ob.Qi) br = int(x);
-            if (br < 0) continue;
-            pairs.push_back({int(c), int(bi), br, so, si, nx});
-            nx += (long long)cl.states.size() * H.bL.dim[H.sL[so]] * pad8(H.bR.dim[H.sR[si]]);
-        }
+    for (const auto& hp : H.pairs) {
+        pairs.push_back({hp.c, hp.bl, hp.br, hp.s_out, hp.s_in, nx});
+        nx += (long long)H.OL.cls[hp.c].states.size() * H.bL.dim[H.sL[hp.s_out]] * pad8(H.bR.dim[H.sR[hp.s_in]]);
     }
+    std::stable_sort(pairs.begin(), pairs.end(), [&](const Pair& a, const Pair& b) {
+        return H.bL.dim[H.sL[a.si]] > H.bL.dim[H.sL[b.si]];
+    });
     P.nx = std::max(nx, 8LL);
     P.x.ensure_cached(size_t(P.nx) * NS * 2, st);
     // ---- tensor maps: one per operand, the NS slice planes as outer dimension
@@ -1078,8 +1073,7 @@ template <int MODE> void build_plan(Ctx& C) {
     P.issued_p2 = issued(w2);
     // persistent CTAs take items round-robin: longest first evens out the tail
     auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
-    std::stable_sort(w1.begin(), w1.end(), longer);
-    std::stable_sort(w2.begin(), w2.end(), longer);
+    std::stable_sort(w2.begin(), w2.end(), longer);  // (w1 is longest first by construction)
     const double t2 = wall_ms();
     // ---- upload
     upload_vec(P.maps, maps, st);
