@@ -338,7 +338,9 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * gbd_step: environments resident, enlargement, Davidson, density matrices
  * and eigensolves, renormalisation, next start vector, IO scheduling, then
  * the enlargement planning (host) in three parts: coefficient links, output
- * blocks, copy and GEMM items.  *n gets the count; out may be NULL. */
+ * blocks, copy and GEMM items, then the algorithmic GB the GBD_MIXED_BF16X3
+ * products moved (each operand, X and psi once per product).  *n gets the
+ * count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

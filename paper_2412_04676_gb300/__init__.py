@@ -356,7 +356,8 @@ class Context:
               "products_sliced_n", "tc_sliced_issued_gflop", "tc_prep_split", "tc_prep_plan", "tc_prep_upload",
               "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop", "renorm_tc_gflop",
               "enlarge_tc_gflop", "step_resident", "step_enlarge", "step_davidson", "step_rho_eig", "step_renorm",
-              "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items"]
+              "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
+              "products_bf16x3_gbytes"]
 
     def timers(self):
         out = np.zeros(64)

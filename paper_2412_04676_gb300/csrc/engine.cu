@@ -950,6 +950,7 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     C.timers[Ctx::T_PROD_MS0 + precision] += ms;
     C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
     C.timers[Ctx::T_PROD_GF0 + precision] += H.flops * 1e-9;
+    if (precision == GBD_MIXED_BF16X3) C.timers[Ctx::T_PROD_GB1] += H.mixed_bytes * 1e-9;
 }
 
 void heff_diag(Ctx& C) {

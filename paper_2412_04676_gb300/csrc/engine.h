@@ -118,7 +118,7 @@ struct Ctx {
            T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
            // device time of the phases of gbd_step on the compute stream (host gaps included)
            T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
-           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_COUNT };
+           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};

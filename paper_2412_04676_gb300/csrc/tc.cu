@@ -1023,6 +1023,11 @@ template <int MODE> void build_plan(Ctx& C) {
         for (int si : seg_of_out[q]) { s2o.push_back(s2[si]); nchunk += s2[si].nchunk; }
         int nseg = int(s2o.size()) - seg0;
         const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
+        // one reduction (and a run of partials) per output tile; the items are
+        // listed K range by K range, so the tiles of one sector that read the
+        // same K chunks of X and O^xR run side by side and share them in L2
+        const int nrange = int((nchunk + target - 1) / target);
+        const size_t r0 = red.size();
         for (int m0 = 0; m0 < mL; m0 += BM)
             for (int n0 = 0; n0 < mR; n0 += TBN) {
                 Reduce r{};
@@ -1034,26 +1039,29 @@ template <int MODE> void build_plan(Ctx& C) {
                 r.N = mR;
                 r.bn = TBN;
                 r.p0 = int(npart);
-                for (int c0 = 0; c0 < nchunk; c0 += int(target)) {
-                    Work w{};
-                    w.m0 = m0;
-                    w.n0 = n0;
-                    w.M = mL;
-                    w.N = mR;
-                    w.seg0 = seg0;
-                    w.nseg = nseg;
-                    w.c0 = c0;
-                    w.c1 = int(std::min<long long>(nchunk, c0 + target));
-                    w.out_kind = 0;
-                    w.promote = MODE == 0 ? 8 : 1;
-                    w.ldo = TBN;
-                    w.colcap = TBN;
-                    w.out = reinterpret_cast<void*>(npart);  // patched to a pointer below
-                    w2.push_back(w);
-                    ++npart;
-                }
+                npart += nrange;
                 r.p1 = int(npart);
                 red.push_back(r);
+            }
+        for (int k = 0; k < nrange; ++k)
+            for (size_t ti = r0; ti < red.size(); ++ti) {
+                const Reduce& r = red[ti];
+                const int c0 = int(k * target);
+                Work w{};
+                w.m0 = r.m0;
+                w.n0 = r.n0;
+                w.M = mL;
+                w.N = mR;
+                w.seg0 = seg0;
+                w.nseg = nseg;
+                w.c0 = c0;
+                w.c1 = int(std::min<long long>(nchunk, c0 + target));
+                w.out_kind = 0;
+                w.promote = MODE == 0 ? 8 : 1;
+                w.ldo = TBN;
+                w.colcap = TBN;
+                w.out = reinterpret_cast<void*>((long long)r.p0 + k);  // patched to a pointer below
+                w2.push_back(w);
             }
     }
     P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
@@ -1073,7 +1081,7 @@ template <int MODE> void build_plan(Ctx& C) {
     P.issued_p2 = issued(w2);
     // persistent CTAs take items round-robin: longest first evens out the tail
     auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
-    std::stable_sort(w2.begin(), w2.end(), longer);  // (w1 is longest first by construction)
+    (void)longer;  // w1 is longest first by construction; w2 keeps its K-range grouping
     const double t2 = wall_ms();
     // ---- upload
     upload_vec(P.maps, maps, st);
