@@ -199,7 +199,7 @@ class Context:
 
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
-                 mixed_fp64_blocks=True, mixed_polish=2):
+                 mixed_fp64_blocks=False, mixed_polish=2):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision

@@ -61,7 +61,7 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->switch_cut = 0;
     cfg->io_timeout_ms = 120000;
     cfg->seed = 12345;
-    cfg->mixed_fp64_blocks = 1;
+    cfg->mixed_fp64_blocks = 0;
     cfg->mixed_polish = 2;
     return GBD_OK;
 }
