@@ -94,14 +94,18 @@ typedef struct {
                            two central positions)                            */
     int io_timeout_ms;  /* bound on any host wait for an IO event              */
     unsigned long long seed; /* random initial MPS when none is imported       */
-    int mixed_fp64_blocks; /* mixed products: the two block Hamiltonian terms
-                              (H_left x 1, 1 x H_right) run in FP64           */
+    int mixed_fp64_blocks; /* mixed products: 1 = the two block Hamiltonian
+                              terms (H_left x 1, 1 x H_right) run in FP64
+                              beside each BF16x3 product; 0 (default) = on
+                              the tensor cores with the other terms        */
     int mixed_polish;   /* mixed Davidson anchors: at the tolerance or at the
                            rounding floor the Ritz vector gets an accurate
                            product; its Rayleigh quotient and residual decide
                            convergence, else the subspace restarts from it.
                            0: none (energy from mixed products), 1: FP64
-                           products, 2: GBD_SLICED_BF16 products            */
+                           products, 2 (default): GBD_SLICED_BF16 products;
+                           with 2 the mixed form also runs the enlargement
+                           and renormalisation GEMMs in the sliced form     */
 } gbd_config;
 
 typedef struct {
