@@ -1121,7 +1121,6 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     std::vector<double> w, S;
     std::vector<double> hist;  // residual norms, for the mixed-precision stagnation test
     int anchors = 0;
-    bool polished = false;
     int status = GBD_OK;
     while (true) {
         ++iters;
@@ -1160,7 +1159,6 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec;
             if (k == 1 && exact_start && anchors == 0 && iters == 1) {
                 // the residual of the start vector is already exact
-                polished = true;
                 if (rn <= C.cfg.dav_tol) break;
                 anchor = false;
             }
@@ -1183,7 +1181,6 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             axpby(x, r, n, -theta, 1.0, s);
             dots(r, 1, r, d);
             rn = std::sqrt(std::max(0.0, d[0]));
-            polished = true;
             if (rn <= C.cfg.dav_tol || anchors >= 3) break;
             if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
             // restart from the exact pair (x, H x)
@@ -1253,7 +1250,6 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     // normalised Ritz vector becomes the current two-site vector
     dots(x, 1, x, d);
     scale(x, n, 1.0 / std::sqrt(d[0]), s);
-    (void)polished;
     if (prec == GBD_MIXED_BF16X3) C.last_dav_quick = (rn <= C.cfg.dav_tol) && anchors <= 1 && status == GBD_OK;
     C.psi.ensure(size_t(n) * sizeof(double));
     GBD_CHECK_CUDA(cudaMemcpyAsync(C.psi.p, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));

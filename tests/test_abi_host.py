@@ -74,3 +74,23 @@ def test_bond_dimension_is_symmetric_and_quadratic():
     c2.load_integrals(h, eri)
     d2 = [c2.mpo_bond_dim(k) for k in range(L + 1)]
     assert d2[L // 2] == d[L // 2] and d2[L // 2 + 1:] == d[L // 2 + 1:]
+
+
+def test_config_defaults_and_validation():
+    # the mixed form's documented defaults, and the ranges the ABI accepts
+    cfg = g.Config()
+    assert g.lib().gbd_config_default(g.C.byref(cfg)) == 0
+    assert cfg.precision == g.FP64 and cfg.mixed_polish == 2 and cfg.mixed_fp64_blocks == 0
+    with pytest.raises(g.GbdError):
+        g.Context(4, 4, 0, mixed_polish=3)
+    with pytest.raises(g.GbdError):
+        g.Context(4, 4, 0, precision=g.SLICED_BF16)  # a product form, not a context precision
+
+
+def test_timers_match_the_documented_list():
+    # gbd_timers reports exactly the entries the binding names, all zero
+    # before any work (no device needed)
+    c = g.Context(4, 4, 0)
+    t = c.timers()
+    assert list(t) == g.Context.TIMERS
+    assert all(v == 0.0 for v in t.values())
