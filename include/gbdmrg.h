@@ -200,6 +200,16 @@ int gbd_mpo_dense(gbd_ctx* ctx, double* out, size_t cap);
  * neighbouring sites. */
 int gbd_import_site(gbd_ctx* ctx, int site, int kind, int nblocks, const int* meta, const double* data);
 
+/* The inverse of gbd_import_site (MPS checkpoints, Eq. 2): site tensor
+ * `site` in the same block format.  Before the sites reach the device these
+ * are the imported blocks; afterwards the current isometry, which truncations
+ * (a5) replace, read back from the device, one block per (q_left, s) segment.
+ * With meta and data NULL only *kind, *nblocks and *data_len are written;
+ * otherwise meta must hold meta_cap >= *nblocks blocks x 5 ints and data
+ * data_cap >= *data_len doubles, else GBD_ERR_ARG. */
+int gbd_export_site(gbd_ctx* ctx, int site, int* kind, int* nblocks, int* meta, int meta_cap, double* data,
+                    size_t data_cap, size_t* data_len);
+
 /* Builds left environments for cuts 0..b and right environments for cuts
  * L..b+2 from the imported sites (renormalisation, Sec. II.B step 3). */
 int gbd_build_envs(gbd_ctx* ctx, int b);

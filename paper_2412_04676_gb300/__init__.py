@@ -83,6 +83,8 @@ _SIGS = {
     "gbd_mpo_bond_dim": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "gbd_mpo_dense": (C.c_int, [_P, _P, C.c_size_t]),
     "gbd_import_site": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "gbd_export_site": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, C.c_int, _P, C.c_size_t,
+                                  C.POINTER(C.c_size_t)]),
     "gbd_build_envs": (C.c_int, [_P, C.c_int]),
     "gbd_build_tables": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int), C.POINTER(HeffInfo)]),
     "gbd_apply_heff": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_int]),
@@ -244,6 +246,20 @@ class Context:
         for k, (site, kind) in enumerate(zip(sites, kinds)):
             meta, data = site_arrays(site)
             _check(lib().gbd_import_site(self.h, k, kind, meta.shape[0], _ptr(meta), _ptr(data)))
+
+    def export_site(self, k):
+        """(kind, {(q_left, s): block}) of site k, the inverse of import_mps's format."""
+        kind, nb, nd = C.c_int(), C.c_int(), C.c_size_t()
+        _check(lib().gbd_export_site(self.h, k, C.byref(kind), C.byref(nb), None, 0, None, 0, C.byref(nd)))
+        meta = np.zeros((max(nb.value, 1), 5), dtype=np.int32)
+        data = np.zeros(max(nd.value, 1))
+        _check(lib().gbd_export_site(self.h, k, C.byref(kind), C.byref(nb), _ptr(meta), nb.value, _ptr(data), data.size,
+                                     C.byref(nd)))
+        site, off = {}, 0
+        for (qn, qt, s, r, c) in meta[:nb.value]:
+            site[((int(qn), int(qt)), int(s))] = data[off:off + r * c].reshape(r, c).copy()
+            off += r * c
+        return kind.value, site
 
     def build_envs(self, b):
         _check(lib().gbd_build_envs(self.h, b))

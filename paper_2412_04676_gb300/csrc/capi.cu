@@ -132,6 +132,27 @@ int gbd_import_site(gbd_ctx* c, int site, int kind, int nblocks, const int* meta
     });
 }
 
+int gbd_export_site(gbd_ctx* c, int site, int* kind, int* nblocks, int* meta, int meta_cap, double* data,
+                    size_t data_cap, size_t* data_len) {
+    return guard([&] {
+        std::vector<int> m;
+        std::vector<double> d;
+        int k = -1;
+        export_site(ctx(c), site, &k, m, d);
+        const int nb = int(m.size() / 5);
+        if (kind) *kind = k;
+        if (nblocks) *nblocks = nb;
+        if (data_len) *data_len = d.size();
+        if (meta || data) {
+            GBD_REQUIRE(meta && data && meta_cap >= nb && data_cap >= d.size(), GBD_ERR_ARG,
+                        "export buffers too small (sizes written to *nblocks and *data_len)");
+            std::copy(m.begin(), m.end(), meta);
+            std::copy(d.begin(), d.end(), data);
+        }
+        return GBD_OK;
+    });
+}
+
 int gbd_build_envs(gbd_ctx* c, int b) {
     return guard([&] {
         build_envs(ctx(c), b);

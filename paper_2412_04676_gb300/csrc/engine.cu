@@ -652,6 +652,46 @@ void import_site(Ctx& C, int k, int kind, int nblk, const int* meta, const doubl
     C.site_kind[k] = kind;
 }
 
+// Site tensor k in the import format (Eq. 2 blocks): the imported blocks
+// while the sites are not yet on the device, else the current isometry
+// (after truncations) read back from the device.
+void export_site(Ctx& C, int k, int* kind, std::vector<int>& meta, std::vector<double>& data) {
+    GBD_REQUIRE(k >= 0 && k < C.L, GBD_ERR_ARG, "site out of range");
+    GBD_REQUIRE(C.site_kind[k] >= 0, GBD_ERR_STATE, "site was never imported");
+    const Iso& I = C.sites[k];
+    meta.clear();
+    data.clear();
+    if (!I.data.p || I.kind < 0) {
+        *kind = C.site_kind[k];
+        meta = C.site_blocks_meta[k];
+        data = C.site_blocks_data[k];
+        return;
+    }
+    *kind = I.kind;
+    std::vector<double> h(size_t(std::max<long long>(I.total, 1)));
+    GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+    if (I.total > 0) GBD_CHECK_CUDA(cudaMemcpy(h.data(), I.data.p, size_t(I.total) * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t oi = 0; oi < I.out.q.size(); ++oi) {
+        if (I.off[oi] < 0) continue;
+        const int e = I.basis.find(I.out.q[oi]);
+        if (e < 0) continue;
+        const int dout = I.out.dim[oi];
+        for (const auto& sg : I.basis.segs[e]) {
+            if (I.kind == 0) {  // rows: (left bond sector, s) segment; cols: new bond sector
+                const Q ql{I.out.q[oi].n - kQS[sg.s].n, I.out.q[oi].t - kQS[sg.s].t};
+                meta.insert(meta.end(), {ql.n, ql.t, sg.s, sg.size, dout});
+                for (int i = 0; i < sg.size; ++i)
+                    for (int j = 0; j < dout; ++j) data.push_back(h[I.off[oi] + (long long)(sg.off + i) * dout + j]);
+            } else {            // rows: new bond sector; cols: (s, right bond sector) segment
+                const Q ql = I.out.q[oi];
+                meta.insert(meta.end(), {ql.n, ql.t, sg.s, dout, sg.size});
+                for (int i = 0; i < dout; ++i)
+                    for (int j = 0; j < sg.size; ++j) data.push_back(h[I.off[oi] + (long long)(sg.off + j) * dout + i]);
+            }
+        }
+    }
+}
+
 // Bonds from imported blocks, then each site's isometry on the device.
 static void make_iso(Ctx& C, int k, int kind) {
     Iso& I = C.sites[k];

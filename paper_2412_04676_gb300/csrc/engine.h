@@ -131,6 +131,7 @@ void import_site(Ctx& C, int k, int kind, int nblk, const int* meta, const doubl
 void finalize_sites(Ctx& C);
 void build_envs(Ctx& C, int b);
 void setup_heff(Ctx& C, int b);
+void export_site(Ctx& C, int k, int* kind, std::vector<int>& meta, std::vector<double>& data);
 double wall_ms();  // host wall clock in ms
 void step_mark(Ctx& C, int phase);  // phase (a T_PH_* index) starts now on the compute stream
 void step_marks_flush(Ctx& C);      // after the stream is synchronised: accumulate the phase times

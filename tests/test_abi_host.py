@@ -94,3 +94,18 @@ def test_timers_match_the_documented_list():
     t = c.timers()
     assert list(t) == g.Context.TIMERS
     assert all(v == 0.0 for v in t.values())
+
+
+def test_export_site_returns_the_imported_blocks():
+    # before the sites reach the device, export is the exact inverse of import
+    L, N, D = 6, 6, 20
+    h, eri = inputs.make_integrals(L, 11)
+    sites, dims = inputs.make_mps(L, N, 0, D, 12)
+    c = g.Context(L, N, 0, D=D)
+    c.load_integrals(h, eri)
+    c.import_mps(sites, [1] * L)
+    for k in range(L):
+        kind, site = c.export_site(k)
+        assert kind == 1 and set(site) == set(sites[k])
+        for key, blk in sites[k].items():
+            assert np.array_equal(site[key], blk)

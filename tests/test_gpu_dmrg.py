@@ -85,3 +85,35 @@ def test_truncated_sweep_is_variational():
     assert all(e >= e_fci - 1e-9 for e in es)
     assert es[2] <= es[1] + 1e-9 <= es[0] + 2e-9
     assert max(s["max_trunc"] for s in st) > 0
+
+
+def test_export_site_from_device_and_after_truncation():
+    # after the sites reach the device, export reads the isometries back; a
+    # truncation replaces site b by a new left isometry whose columns are
+    # orthonormal per sector (Eq. 2 left-canonical condition)
+    import paper_2412_04676_gb300 as gg
+    L, N, D, b = 8, 8, 40, 3
+    h, eri = inputs.make_integrals(L, 31)
+    sites, dims = inputs.make_mps(L, N, 0, D, 32, n_left=b)
+    kinds = [0] * b + [1] * (L - b)
+    c = gg.Context(L, N, 0, D=D)
+    c.load_integrals(h, eri)
+    c.import_mps(sites, kinds)
+    c.build_envs(b)
+    for k in range(L):
+        kind, site = c.export_site(k)
+        assert kind == kinds[k]
+        ref = {key: blk for key, blk in sites[k].items() if blk.size}
+        assert set(ref) <= set(site)
+        for key, blk in site.items():  # segments the import left out are zero
+            assert np.array_equal(blk, ref[key]) if key in ref else not blk.any()
+    c.step(b, 1, D)
+    kind, site = c.export_site(b)
+    assert kind == 0
+    groups = {}
+    for (ql, s), blk in site.items():  # stack the (q_left, s) segments of each new-bond sector
+        qn = (ql[0] + (0, 1, 1, 2)[s], ql[1] + (0, 1, -1, 0)[s])
+        groups.setdefault(qn, []).append(blk)
+    for qn, blks in groups.items():
+        U = np.vstack(blks)
+        assert np.allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-12)
