@@ -334,8 +334,9 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
 
 /* Accumulated phase timers of the context in ms, in this order: enlargement
  * planning (host), enlargement kernels, renormalisation planning (host),
- * renormalisation kernels, per-sector eigensolves, FP64 polish products,
- * mixed-precision operand preparation, Davidson host time (reserved), then
+ * renormalisation kernels, per-sector eigensolves, Davidson anchor products
+ * (host wall time, operand preparation included), tensor-core operand
+ * preparation, Davidson host time (reserved), then
  * the FP64 GFLOP executed by enlargement and by renormalisation GEMMs, then
  * the tensor-core GFLOP one BF16x3 product of the last prepared H_eff issues
  * in phase 1 and in phase 2 (whole tiles, the three split products; not

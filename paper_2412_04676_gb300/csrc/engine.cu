@@ -1082,8 +1082,8 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     const int kmax = std::max(3, std::min(C.cfg.dav_max_sub, 36));
     const int keep = std::max(1, std::min(C.cfg.dav_keep, kmax - 2));
     const int prec = C.cfg.precision;
-    // a mixed-precision product carries ~1e-5 relative rounding, so its
-    // residual cannot fall much below that; the FP64 polish fixes the energy
+    // a BF16x3 product carries ~1e-5 relative rounding, so its residual cannot
+    // fall much below that; the anchor products (below) fix the energy
     const double tol = prec == GBD_MIXED_BF16X3 ? std::max(C.cfg.dav_tol, 2e-5) : C.cfg.dav_tol;
     heff_diag(C);
     C.dav_V.ensure(size_t(kmax) * n * sizeof(double));
