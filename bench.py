@@ -177,10 +177,15 @@ def run_reference(args, rank, world):
     cpu_t = []
     value, cores, desc, times = oracle_sample(max_steps=args.steps, warmup=args.warmup)
     ms = 1000.0 * sum(times) / len(times)
+    W = WORKLOADS[args.workload]
+    # the same workload name as our arm; each step is a bounded sample of it
+    # (the oracle cannot build the config-2 environments in bounded time)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "oracle sample: L=10 N=10 2Sz=0 D=256 mid-chain H_eff psi",
+            "config": {"workload": (f"L={W['L']} N={W['N']} 2Sz={W['tsz']} D={W['D']} two-site step at the mid-chain cut"
+                                    + (" (config 2)" if args.workload == "config2" else "")),
+                       "sample": "oracle H_eff psi products at L=10 N=10 2Sz=0 D=256 (config 1, mid-chain)",
                        "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
