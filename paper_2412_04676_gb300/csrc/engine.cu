@@ -1233,13 +1233,12 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         }
         if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
         precondition(r, H.diag.as<double>(), theta, t, n, s);
+        // two Gram-Schmidt passes on the device: the projections stay in
+        // `small` (no host round trip), t -= sum_i (V_i . t) V_i
         auto orth = [&](int kk) {
             for (int pass = 0; pass < 2; ++pass) {
-                std::vector<double> c;
-                dots(V, kk, t, c);
-                for (auto& v : c) v = -v;
-                put(c);
-                combine(V, n, kk, small, t, n, 1.0, 1.0, s);
+                multi_dot(V, n, kk, t, n, small, part, s);
+                combine(V, n, kk, small, t, n, -1.0, 1.0, s);
             }
         };
         orth(k);
