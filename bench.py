@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "config2": dict(L=30, N=30, tsz=0, D=1024, seed=1002, b=14),
+    "l30_d1024": dict(L=30, N=30, tsz=0, D=1024, seed=1002, b=14),
     # a few-GB case of the same kernels, for profiler captures
     "small": dict(L=16, N=16, tsz=0, D=512, seed=1002, b=7),
 }
@@ -157,7 +157,7 @@ def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
         cores = max(int(x.get("num_threads", 0)) for x in threadpool_info()) or cores
     except Exception:
         pass
-    desc = (f"oracle H_eff psi at L=10,N=10,D=256 (config 1, mid-chain cut), dim {He.dim}, "
+    desc = (f"oracle H_eff psi at L=10,N=10,D=256 (mid-chain cut), dim {He.dim}, "
             f"{len(times)} products in {sum(times):.1f} s; the oracle cannot build the L=30, D=1024 "
             f"environments in bounded time")
     return flops * len(times) / sum(times) / 1e12, cores, desc, times
@@ -183,9 +183,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": (f"L={W['L']} N={W['N']} 2Sz={W['tsz']} D={W['D']} two-site step at the mid-chain cut"
-                                    + (" (config 2)" if args.workload == "config2" else "")),
-                       "sample": "oracle H_eff psi products at L=10 N=10 2Sz=0 D=256 (config 1, mid-chain)",
+            "config": {"workload": f"L={W['L']} N={W['N']} 2Sz={W['tsz']} D={W['D']} two-site step at the mid-chain cut",
+                       "sample": "oracle H_eff psi products at L=10 N=10 2Sz=0 D=256 (mid-chain)",
                        "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -384,7 +383,7 @@ def run_ours(args, rank, world, local_rank):
         n = forms["bf16x3"]["products"]
         gb = dt["products_bf16x3_gbytes"]
         gbs = gb / (forms["bf16x3"]["ms"] * 1e-3)
-        # arithmetic intensity 3 F / bytes (~140 bf16 flop/B at config 2) is below
+        # arithmetic intensity 3 F / bytes (~140 bf16 flop/B at L=30, D=1024) is below
         # the machine balance (bf16 peak / HBM, ~280 flop/B): the product is
         # HBM-bound, so its roofline is the algorithmic bytes over time
         roofs["bf16x3"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -437,8 +436,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_dev_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == g.FP64 else "bf16->f32",
         "data": "synthetic",
-        "config": {"workload": (f"L={L} N={N} 2Sz={tsz} D={D} two-site step at the mid-chain cut"
-                                + (" (config 2)" if args.workload == "config2" else "")),
+        "config": {"workload": f"L={L} N={N} 2Sz={tsz} D={D} two-site step at the mid-chain cut",
                    "precision": args.precision, "offload": not args.no_offload,
                    "environments": "renormalised on the GPU from a seeded random isometric MPS with the "
                                    "D=1024 sector distribution",
@@ -477,7 +475,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="l30_d1024")
     ap.add_argument("--no-offload", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -279,8 +279,11 @@ int gbd_step_energies(gbd_ctx* ctx, double* out, int cap, int* n);
  * right block (cut c, orbitals c..L-1).
  *
  * gbd_pack_env serialises one resident environment into dst (host or device
- * memory, flagged) as self-contained packages (format in the design doc of the
- * source tree: 64-byte header + payload, 16-byte aligned, checksum).  If cap
+ * memory, flagged) as self-contained packages (Sec. III.B.3), one per class
+ * block: a 64-byte header (magic "GBDP", version, dtype, side, cut, package
+ * count and index, class, layers, q_out, q_in, rows, cols, arena offset,
+ * checksum sum_i w_i (2i + 1) mod 2^64 over the payload words) followed by
+ * the FP64 payload padded to 16 bytes.  If cap
  * is too small, returns GBD_ERR_ARG and writes the exact required size to
  * *bytes (size prediction, Sec. III.B.2).  */
 int gbd_pack_env(gbd_ctx* ctx, int side, int cut, void* dst, size_t cap, size_t* bytes, int dst_on_device);

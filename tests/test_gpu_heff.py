@@ -55,7 +55,7 @@ def test_heff_ragged_and_large_sectors_span_tiles():
         assert np.abs(y - y_ref).max() <= TOL * np.abs(y_ref).max()
 
 
-def test_heff_hermitian_full_size_config2():
+def test_heff_hermitian_full_size_l30_d1024():
     # L=30, N=30, D=1024 at the mid-chain cut: properties that hold at any size
     L, N, tsz, D, b = 30, 30, 0, 1024, 14
     c = heff_case(L, N, tsz, D, 1002, b, oracle=False)

@@ -83,7 +83,7 @@ def test_mixed_sweep_energy_within_1e6(polish):
     assert abs(out[g.MIXED_BF16X3] - out[g.FP64]) <= 1e-6, out
 
 
-def test_mixed_product_full_size_config2():
+def test_mixed_product_full_size_l30_d1024():
     # L=30, N=30, D=1024 at the mid-chain cut (the bench's launch configuration):
     # mixed vs the FP64 product of the same library, relative norm error and
     # the symmetry of the mixed operator (properties that hold at any size)

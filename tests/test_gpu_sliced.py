@@ -117,7 +117,7 @@ def test_sliced_anchor_sweep_energy():
     assert abs(out[g.MIXED_BF16X3] - out[g.FP64]) <= 1e-7, out
 
 
-def test_sliced_product_full_size_config2():
+def test_sliced_product_full_size_l30_d1024():
     # L=30, N=30, D=1024 at the mid-chain cut (the bench's launch configuration):
     # sliced vs the FP64 product of the same library, relative norm error and
     # the symmetry of the sliced operator (properties that hold at any size)
