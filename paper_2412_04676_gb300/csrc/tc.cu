@@ -1067,9 +1067,8 @@ template <int MODE> void build_plan(Ctx& C) {
     };
     P.issued_p1 = issued(w1);
     P.issued_p2 = issued(w2);
-    // persistent CTAs take items round-robin: longest first evens out the tail
-    auto longer = [](const Work& x, const Work& y) { return x.c1 - x.c0 > y.c1 - y.c0; };
-    (void)longer;  // w1 is longest first by construction; w2 keeps its K-range grouping
+    // persistent CTAs take items round-robin: w1 is longest first by
+    // construction (pairs sorted by K), w2 keeps its K-range grouping
     const double t2 = wall_ms();
     // ---- upload
     upload_vec(P.maps, maps, st);
