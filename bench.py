@@ -32,11 +32,29 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    # the smallest configuration (the oracle runs it in seconds): like-for-like pair with --impl reference
+    "l10_d256": dict(L=10, N=10, tsz=0, D=256, seed=1001, b=4),
     "l30_d1024": dict(L=30, N=30, tsz=0, D=1024, seed=1002, b=14),
     # a few-GB case of the same kernels, for profiler captures
     "small": dict(L=16, N=16, tsz=0, D=512, seed=1002, b=7),
 }
-METRIC = "H_eff psi useful TFLOP/s (two-site DMRG step, L=30 N=30 D=1024 mid-chain)"
+DEFAULT_WORKLOAD = "l30_d1024"
+METRIC = "H_eff psi useful TFLOP/s over whole two-site DMRG steps (mixed BF16x3 form, |dE| <= 1e-6 Eh)"
+
+# DRAM traffic of one BF16x3 H_eff product (phase-1 + phase-2 kernels) from
+# one ncu capture of a small case, scaled to the workload by its operator
+# bytes; valid only while the kernel source is the one that was measured.
+TRAFFIC = {}
+
+
+def workload_name(W):
+    return f"L={W['L']} N={W['N']} 2Sz={W['tsz']} D={W['D']} two-site steps around the mid-chain cut {W['b']}"
+
+
+def src_hash(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- clocks
@@ -114,9 +132,9 @@ def sweep_compare(spec):
 
 # ---------------------------------------------------------------- oracle leg
 def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
-    """The oracle's H_eff psi on L=10, N=10, D=256 (mid-chain), timed on host cores.
+    """The oracle's H_eff psi at L=10, N=10, D=256 (mid-chain cut 4), timed on host cores.
 
-    Returns (useful TFLOP/s, cores, description, per-step seconds).
+    Returns (useful TFLOP/s, cores, description, per-product seconds).
     """
     import numpy as np
 
@@ -125,7 +143,8 @@ def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
     from oracle import hamiltonian as H
     from oracle import mpo as M
 
-    L, N, tsz, D, b, seed = 10, 10, 0, 256, 4, 1001
+    W = WORKLOADS["l10_d256"]
+    L, N, tsz, D, b, seed = W["L"], W["N"], W["tsz"], W["D"], W["b"], W["seed"]
     h, eri = inputs.make_integrals(L, seed)
     mp = M.MPO(L, H.hamiltonian_terms(h, eri))
     sites, dims = inputs.make_mps(L, N, tsz, D, seed + 1, n_left=b)
@@ -157,9 +176,8 @@ def oracle_sample(seconds=20.0, max_steps=None, warmup=0):
         cores = max(int(x.get("num_threads", 0)) for x in threadpool_info()) or cores
     except Exception:
         pass
-    desc = (f"oracle H_eff psi at L=10,N=10,D=256 (mid-chain cut), dim {He.dim}, "
-            f"{len(times)} products in {sum(times):.1f} s; the oracle cannot build the L=30, D=1024 "
-            f"environments in bounded time")
+    desc = (f"oracle H_eff psi products at L=10 N=10 2Sz=0 D=256 (mid-chain cut 4), dim {He.dim}, "
+            f"{len(times)} products in {sum(times):.1f} s")
     return flops * len(times) / sum(times) / 1e12, cores, desc, times
 
 
@@ -172,23 +190,27 @@ def _oracle_child(q, seconds):
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle timed on the host cores: H_eff psi products at L=10, D=256.
+
+    The oracle cannot build the environments of the larger workloads in
+    bounded time, so its line always names the L=10 workload it ran; with
+    --workload l10_d256 both arms run the same workload (like for like).
+    """
     if rank != 0:
         return 0
-    cpu_t = []
     value, cores, desc, times = oracle_sample(max_steps=args.steps, warmup=args.warmup)
     ms = 1000.0 * sum(times) / len(times)
-    W = WORKLOADS[args.workload]
-    # the same workload name as our arm; each step is a bounded sample of it
-    # (the oracle cannot build the config-2 environments in bounded time)
+    ran = WORKLOADS["l10_d256"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"L={W['L']} N={W['N']} 2Sz={W['tsz']} D={W['D']} two-site step at the mid-chain cut",
-                       "sample": "oracle H_eff psi products at L=10 N=10 2Sz=0 D=256 (mid-chain)",
-                       "parallelism": "host cores"},
+            "config": {"workload": f"L={ran['L']} N={ran['N']} 2Sz={ran['tsz']} D={ran['D']} H_eff psi products "
+                                   f"at the mid-chain cut {ran['b']} (oracle, FP64, host cores)",
+                       "same_config_as_gpu_arm": args.workload == "l10_d256",
+                       "gpu_arm_workload": workload_name(WORKLOADS[args.workload]),
+                       "step": "one oracle H_eff psi product", "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    del cpu_t
     print(json.dumps(line), flush=True)
     return 0
 
@@ -208,11 +230,30 @@ def job_value(world, flops_per_rank, ms):
     """Whole-job useful TFLOP/s: flops of all replicas over the slowest time."""
     return world * flops_per_rank / (ms * 1e-3) / 1e12
 
+def host_link_peak(device, nbytes=1 << 30, reps=5):
+    """Pinned host <-> device copy bandwidth (plain cudaMemcpyAsync through torch), best of reps."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    out = {}
+    for name, (dst, src) in (("d2h_gbs", (h, d)), ("h2d_gbs", (d, h))):
+        best = 0.0
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            b.synchronize()
+            best = max(best, nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+        out[name] = best
+    out["bytes"] = nbytes
+    out["how"] = "pinned host <-> device cudaMemcpyAsync of 1 GiB, best of 5"
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import multiprocessing as mp_
-
-    cpu_q = None
-    cpu_proc = None
 
     import numpy as np
     import torch
@@ -221,6 +262,8 @@ def run_ours(args, rank, world, local_rank):
     import paper_2412_04676_gb300 as g
     from paper_2412_04676_gb300 import build
 
+    cpu_q = None
+    cpu_proc = None
     torch.cuda.set_device(local_rank)
     build.build()
     W = WORKLOADS[args.workload]
@@ -228,6 +271,7 @@ def run_ours(args, rank, world, local_rank):
     prec = g.MIXED_BF16X3 if args.precision == "mixed" else g.FP64
     h, eri = inputs.make_integrals(L, W["seed"])
     sites, dims = inputs.make_mps(L, N, tsz, D, W["seed"] + 1 + rank, n_left=b)
+
     def make_ctx():
         c = g.Context(L, N, tsz, D=D, precision=prec, offload=not args.no_offload, device=local_rank,
                       dav_tol=args.tol, dav_max_matvec=args.max_matvec)
@@ -278,9 +322,19 @@ def run_ours(args, rank, world, local_rank):
     nmv = sum(s["matvecs"] for s in stats)
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_src = "of measured"
     except Exception:
         peaks = {}
-    hbm = peaks.get("hbm_gbs", 6787.2)
+        peak_src = "of fallback"
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16_burst = peaks.get("bf16_tflops", 1900.0)
+    bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)
+    # host link (NVLink-C2C) peak for the offload fraction
+    link = None
+    try:
+        link = host_link_peak(f"cuda:{local_rank}")
+    except Exception as e:  # measurement extra; never fatal
+        link = {"error": repr(e)}
     # pack kernel throughput: HBM -> HBM on the environment the last step
     # produced, and the offload saves of the timed steps (pinned host memory)
     pack = None
@@ -290,6 +344,10 @@ def run_ours(args, rank, world, local_rank):
         io = ctx.io_stats()
         pk = {"offload_bytes": io["bytes_d2h"], "offload_ms": io["ms_save"],
               "offload_gbs": io["bytes_d2h"] / (io["ms_save"] * 1e-3) / 1e9 if io["ms_save"] > 0 else None}
+        if pk["offload_gbs"] and link and link.get("d2h_gbs"):
+            pk["offload_roofline"] = {"bound": "host link", "achieved": pk["offload_gbs"], "peak": link["d2h_gbs"],
+                                      "unit": "GB/s", "frac": pk["offload_gbs"] / link["d2h_gbs"],
+                                      "peak_source": "measured here: " + link["how"]}
         if nbytes > 0:
             dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
             ctx.pack_env(side, cut, dev)
@@ -301,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
             gbs = 2 * nbytes / (ms * 1e-3) / 1e9
             pk.update({"bytes": nbytes, "hbm_ms": ms,
                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                    "peak_source": f"{peak_src}: HBM copy bandwidth",
                                     "note": "read + write bytes of one packed environment, device to device"}})
         pack = pk
     except Exception as e:  # measurement extra; never fatal
@@ -344,26 +403,14 @@ def run_ours(args, rank, world, local_rank):
         cpu_proc = ctx_mp.Process(target=_oracle_child, args=(cpu_q, args.cpu_seconds), daemon=True)
         cpu_proc.start()
     ms_dev_max, e2e_max = job_times(ms_dev, e2e_ms, world, "cuda")
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        peaks = {}
-    hbm = peaks.get("hbm_gbs", 6787.2)
     value = job_value(world, flops, ms_dev_max)
     e2e_value = job_value(world, e2e_flops, e2e_max)
     if rank != 0:
         return 0
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
     flops_mv = info["useful_flops"]
     dt = {k: tm1[k] - tm0[k] for k in tm1}
     for k in ("tc_issued_gflop_p1", "tc_issued_gflop_p2", "tc_sliced_issued_gflop"):
         dt[k] = tm1[k]  # per product of the last prepared position, not accumulated
-    hbm = peaks.get("hbm_gbs", 6787.2)
-    bf16 = peaks.get("bf16_tflops", 1908.5)
     # H_eff products of the timed steps by form (device time from the library)
     forms = {}
     for key in ("fp64", "bf16x3", "sliced"):
@@ -379,30 +426,36 @@ def run_ours(args, rank, world, local_rank):
                          "kernel": "gemm_f64_kernel: FP64 H_eff product (phase-1 + phase-2 launches)",
                          "peak_source": "of measured: cuBLAS DGEMM 8192^3 on this pool"}
     if "bf16x3" in forms:
-        a = forms["bf16x3"]["useful_tflops"]
-        n = forms["bf16x3"]["products"]
-        gb = dt["products_bf16x3_gbytes"]
-        gbs = gb / (forms["bf16x3"]["ms"] * 1e-3)
-        # arithmetic intensity 3 F / bytes (~140 bf16 flop/B at L=30, D=1024) is below
-        # the machine balance (bf16 peak / HBM, ~280 flop/B): the product is
-        # HBM-bound, so its roofline is the algorithmic bytes over time
-        roofs["bf16x3"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                           "traffic": None, "ms": forms["bf16x3"]["ms"],
-                           "bytes_per_launch_pair": gb / n * 1e9,
-                           "kernel": "tc_gemm_kernel<0, 1> + <0, 2>: BF16x3 H_eff product (split, phase 1, phase 2, reduce)",
-                           "peak_source": "of measured: HBM copy bandwidth",
-                           "intensity_flop_per_byte": 3.0 * forms["bf16x3"]["useful_gflop"] / gb if gb else None,
-                           "tensor_view": {"achieved": a, "peak": bf16 / 3.0, "unit": "TFLOP/s", "frac": a / (bf16 / 3.0),
-                                           "peak_source": "of measured: bf16 burst / 3 (three split products per useful flop)"},
-                           "issued_tflops": (dt["tc_issued_gflop_p1"] + dt["tc_issued_gflop_p2"]) * n
-                                            / forms["bf16x3"]["ms"],
-                           "issued_note": "bf16 MMA flops of whole 128-row tiles at the MMA width, padding included"}
+        f = forms["bf16x3"]
+        a, n = f["useful_tflops"], f["products"]
+        gb, xgb = dt["products_bf16x3_gbytes"], dt["products_bf16x3_x_gbytes"]
+        peak = bf16_sust / 3.0
+        tr = TRAFFIC.get(args.workload)
+        traffic = None
+        if tr and tr.get("tc_cu") == src_hash("paper_2412_04676_gb300/csrc/tc.cu"):
+            traffic = tr["bytes_per_product"]
+        roofs["bf16x3"] = {
+            "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+            "traffic": traffic, "ms": f["ms"], "launches": n,
+            "kernel": "tc_gemm_kernel<0, 1> + <0, 2> (+ split, reduce): BF16x3 H_eff product",
+            "peak_source": f"{peak_src}: bf16 sustained / 3 (three split products per useful flop; "
+                           "the product is timed inside whole steps)",
+            "algorithmic_bytes_per_product": gb / n * 1e9,
+            "bytes_note": "operators read once as BF16 hi+lo (4 B/element), psi in and H psi out (FP64)",
+            "hbm_view": {"achieved": gb / (f["ms"] * 1e-3), "peak": hbm, "unit": "GB/s",
+                         "frac": gb / (f["ms"] * 1e-3) / hbm, "peak_source": f"{peak_src}: HBM copy bandwidth"},
+            "x_overhead_bytes_per_product": xgb / n * 1e9,
+            "x_overhead_note": "phase-1 intermediate X written and read once (BF16 hi+lo), not algorithmic",
+            "intensity_flop_per_byte": 3.0 * f["useful_gflop"] / gb if gb else None,
+            "ridge_flop_per_byte": bf16_sust * 1e3 / hbm,
+            "issued_tflops": (dt["tc_issued_gflop_p1"] + dt["tc_issued_gflop_p2"]) * n / f["ms"],
+            "issued_note": "bf16 MMA flops of whole 128-row tiles at the MMA width, padding included"}
     if "sliced" in forms:
         a = forms["sliced"]["useful_tflops"]
-        roofs["sliced"] = {"bound": "tensor", "achieved": a, "peak": bf16 / 10.0, "unit": "TFLOP/s",
-                           "frac": a / (bf16 / 10.0), "traffic": None, "ms": forms["sliced"]["ms"],
+        roofs["sliced"] = {"bound": "tensor", "achieved": a, "peak": bf16_sust / 10.0, "unit": "TFLOP/s",
+                           "frac": a / (bf16_sust / 10.0), "traffic": None, "ms": forms["sliced"]["ms"],
                            "kernel": "tc_gemm_kernel<1>: sliced H_eff product, Davidson anchors",
-                           "peak_source": "of measured: bf16 burst / 10 (ten slice products per useful flop)",
+                           "peak_source": f"{peak_src}: bf16 sustained / 10 (ten slice products per useful flop)",
                            "issued_tflops": dt["tc_sliced_issued_gflop"] * forms["sliced"]["products"]
                                             / forms["sliced"]["ms"]}
     env_ms = dt["enlarge_dev"] + dt["renorm_dev"]
@@ -410,8 +463,6 @@ def run_ours(args, rank, world, local_rank):
         gf64 = dt["enlarge_gflop"] + dt["renorm_gflop"]
         gftc = dt["renorm_tc_gflop"] + dt["enlarge_tc_gflop"]
         a = (gf64 + gftc) / env_ms
-        # FP64 GEMMs bound by the FP64 pipe; with a tensor-core share the rate is
-        # reported without a single roofline
         roofs["environments"] = {"bound": "alu" if gftc == 0 else "alu+tensor", "achieved": a,
                                  "peak": args.fp64_peak if gftc == 0 else None, "unit": "TFLOP/s",
                                  "frac": a / args.fp64_peak if gftc == 0 else None, "traffic": None, "ms": env_ms,
@@ -426,23 +477,29 @@ def run_ours(args, rank, world, local_rank):
         try:
             r = cpu_q.get(timeout=args.cpu_seconds + 240)
             if r and r[0] != "error":
-                cpu = {"value": r[0], "unit": "TFLOP/s", "cores": r[1], "kind": "oracle", "sample": r[2]}
+                cpu = {"value": r[0], "unit": "TFLOP/s", "cores": r[1], "kind": "oracle", "sample": r[2],
+                       "same_config": args.workload == "l10_d256"}
             else:
                 cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": str(r)}
         except Exception as e:
             cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": f"timeout {e!r}"}
+    status = [s["dav_status"] for s in stats]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_dev_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == g.FP64 else "bf16->f32",
         "data": "synthetic",
-        "config": {"workload": f"L={L} N={N} 2Sz={tsz} D={D} two-site step at the mid-chain cut",
+        "config": {"workload": workload_name(W),
                    "precision": args.precision, "offload": not args.no_offload,
                    "environments": "renormalised on the GPU from a seeded random isometric MPS with the "
-                                   "D=1024 sector distribution",
-                   "l2": "operands larger than L2 (enlarged operators > 1 GB)",
+                                   f"D={D} sector distribution",
+                   "l2": "operands larger than L2 (enlarged operators > 1 GB)" if info["operator_bytes"] > 2e9
+                         else "small workload: operands may fit in L2",
                    "parallelism": f"replicas x{world}", "psi_dim": info["dim"], "n_terms": info["n_terms"],
-                   "useful_gflop_per_product_at_start": flops_mv / 1e9},
+                   "useful_gflop_per_product_at_start": flops_mv / 1e9,
+                   "device_memory_model_gb": {k: info[k] / 1e9 for k in ("mem_operators", "mem_planes_bf16x3",
+                                                                          "mem_planes_sliced", "mem_x_fp64",
+                                                                          "mem_x_tensor")}},
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(l1 - l0),
@@ -450,16 +507,22 @@ def run_ours(args, rank, world, local_rank):
         "roofline_all": roofs,
         "cpu_baseline": cpu,
         "clocks": clk,
+        "davidson": {"converged_steps": sum(1 for x in status if x == 0), "steps": len(status),
+                     "status_per_step": status, "matvecs_per_step": [s["matvecs"] for s in stats],
+                     "resid_per_step": [s["resid"] for s in stats], "max_matvec": args.max_matvec,
+                     "tol": args.tol},
+        "host_link": link,
         "pack": pack,
         "sweep": sweep,
-        "detail": {"matvec_tflops": flops / (ms_mv * 1e-3) / 1e12 if ms_mv else 0.0, "matvecs": nmv, "ms_matvec": ms_mv, "ms_device": ms_dev,
+        "detail": {"matvec_tflops": flops / (ms_mv * 1e-3) / 1e12 if ms_mv else 0.0, "matvecs": nmv,
+                   "ms_matvec": ms_mv, "ms_device": ms_dev,
                    "wall_s": t_wall, "energy": stats[-1]["energy"],
                    "ms_io_exposed": sum(s["ms_io_exposed"] for s in stats),
                    "bytes_packed_per_step": sum(s["bytes_packed"] for s in stats) / args.steps,
                    "ms_truncate": sum(s["ms_truncate"] for s in stats),
                    "ms_renorm": sum(s["ms_renorm"] for s in stats),
                    "timers_ms": dt, "products": forms,
-                   "steps_matvecs": [s["matvecs"] for s in stats], "e2e_steps_matvecs": [s["matvecs"] for s in e2e_stats],
+                   "e2e_steps_matvecs": [s["matvecs"] for s in e2e_stats],
                    "e2e_steps_ms": [s["ms_device"] for s in e2e_stats]},
     }
     print(json.dumps(line), flush=True)
@@ -475,12 +538,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="l30_d1024")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-offload", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--max-matvec", type=int, default=40)
+    ap.add_argument("--max-matvec", type=int, default=60)
     ap.add_argument("--fp64-peak", type=float, default=1.0975)
     ap.add_argument("--sweep-config", default="14,14,384,4",
                     help="L,N,D,sweeps of the FP64-vs-mixed sweep comparison ('' to skip)")

@@ -28,7 +28,9 @@
  * order, each followed by the states of cut-(b+2) sector Q + q_s.
  *
  * Status: every call returns int: 0 = OK, < 0 = error, > 0 = warning.
- * gbd_last_error() gives a thread-local message for the last failure.  No
+ * gbd_last_error() gives the message of the last failed call made by the
+ * calling thread, whatever context it was made on; it takes no context
+ * because some failures (gbd_create, gbd_pack_noalloc) have none.  No
  * exception crosses the ABI and no device code traps.
  *
  * Ownership: the library owns all device memory and pinned host memory it
@@ -106,7 +108,28 @@ typedef struct {
                            products, 2 (default): GBD_SLICED_BF16 products;
                            with 2 the mixed form also runs the enlargement
                            and renormalisation GEMMs in the sliced form     */
+    int fault_inject;   /* host-side fault injection for failure tests, 0 in
+                           normal use; a sum of GBD_FAULT_* bits           */
+    int low_memory;     /* mixed form with sliced anchors (mixed_polish = 2):
+                           its products read only the tensor-core planes, so
+                           the FP64 enlarged operators can be released once
+                           both forms' planes are built (the diagonal first).
+                           0 (default): only when the planes and the phase-1
+                           buffer would not fit beside them; 1: always;
+                           -1: never.  A later GBD_FP64 product at the same
+                           position enlarges the operators again.          */
 } gbd_config;
+
+/* Host-side fault injection (gbd_config.fault_inject).  Each failure is made
+ * on the host; no device code is made to fault, trap or hang.
+ *   GBD_FAULT_PINNED_ALLOC: every pinned host allocation of the offload
+ *     store is refused -> GBD_ERR_HOST_OOM from the call that needed it.
+ *   GBD_FAULT_IO_NEVER_READY: host waits on IO events never see them
+ *     complete, so each runs out after io_timeout_ms -> GBD_ERR_TIMEOUT.
+ *   GBD_FAULT_CORRUPT_HOST_COPY: before an offloaded environment is loaded
+ *     back, one payload byte of its host copy is flipped -> the package
+ *     checksum fails when the environment is first used (GBD_ERR_CORRUPT). */
+enum { GBD_FAULT_PINNED_ALLOC = 1, GBD_FAULT_IO_NEVER_READY = 2, GBD_FAULT_CORRUPT_HOST_COPY = 4 };
 
 typedef struct {
     int n, tsz;         /* quantum numbers of the sector                        */
@@ -122,10 +145,20 @@ typedef struct {
     long long n_gemm;       /* sector GEMMs in one product (both phases)         */
     double useful_flops;    /* 2*m*k*n summed over those GEMMs, counted once     */
     double operator_bytes;  /* FP64 bytes of the two enlarged operator sets      */
-    double mixed_bytes;     /* algorithmic HBM bytes of one mixed product:
-                               BF16 hi+lo operands (4 B/element), the phase-1
-                               intermediate written and read once (4 B each),
-                               psi read and H psi written (FP64)                */
+    double mixed_bytes;     /* algorithmic HBM bytes of one GBD_MIXED_BF16X3
+                               product: every operator element read once as
+                               BF16 hi + lo (4 B), psi read and H psi written
+                               (FP64, 8 B each)                                */
+    double mixed_x_bytes;   /* overhead traffic of the two-phase form on top of
+                               mixed_bytes: the phase-1 intermediate X written
+                               and read once as BF16 hi + lo (8 B per element) */
+    /* Device memory model of the position (bytes), from the tables: */
+    double mem_operators;   /* FP64 arenas of the two enlarged operator sets    */
+    double mem_planes_bf16x3; /* BF16 hi/lo operator planes (rows padded to 8)  */
+    double mem_planes_sliced; /* four BF16 slice planes of the operators        */
+    double mem_x_fp64;      /* phase-1 intermediate of the FP64 form            */
+    double mem_x_tensor;    /* phase-1 intermediate of the tensor-core forms
+                               (one buffer shared by both: four slice planes)  */
 } gbd_heff_info;
 
 typedef struct {
@@ -167,6 +200,8 @@ typedef struct {
     double useful_flops;    /* H_eff useful flops of the step                    */
     double bytes_packed;    /* environment bytes serialised to host this step    */
     double ms_device;       /* CUDA-event span of the step on the compute stream */
+    int dav_status;         /* GBD_OK: Davidson converged; GBD_WARN_NOT_CONVERGED:
+                               it stopped at its product limit              */
 } gbd_step_stats;
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -203,7 +238,8 @@ int gbd_import_site(gbd_ctx* ctx, int site, int kind, int nblocks, const int* me
 /* The inverse of gbd_import_site (MPS checkpoints, Eq. 2): site tensor
  * `site` in the same block format.  Before the sites reach the device these
  * are the imported blocks; afterwards the current isometry, which truncations
- * (a5) replace, read back from the device, one block per (q_left, s) segment.
+ * (Sec. II.B step 3) replace, read back from the device, one block per
+ * (q_left, s) segment.
  * With meta and data NULL only *kind, *nblocks and *data_len are written;
  * otherwise meta must hold meta_cap >= *nblocks blocks x 5 ints and data
  * data_cap >= *data_len doubles, else GBD_ERR_ARG. */
@@ -214,13 +250,13 @@ int gbd_export_site(gbd_ctx* ctx, int site, int* kind, int* nblocks, int* meta, 
  * L..b+2 from the imported sites (renormalisation, Sec. II.B step 3). */
 int gbd_build_envs(gbd_ctx* ctx, int b);
 
-/* --------------------------------------------------------------- tables a1 */
+/* ---------------------------------- sector tables (Sec. II.B, Fig. 4a) */
 /* Sector table of the wavefunction at two-site position b (needs
  * gbd_build_envs or a sweep position at b).  Writes up to cap sectors to
  * out, the count to *n, and the product statistics to *info. */
 int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n, gbd_heff_info* info);
 
-/* ------------------------------------------------------------ hot path a3 */
+/* ------------------------------- H_eff psi (Sec. II.B step 2, Eq. 3) */
 /* psi_out = H_eff psi_in at position b (Sec. II.B step 2).  Vectors in the
  * sector-major layout above, FP64.  on_device = 1: both pointers are device
  * pointers; 0: host pointers (copied in and out).  precision selects the
@@ -231,17 +267,18 @@ int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, i
 /* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
 int gbd_heff_diagonal(gbd_ctx* ctx, int b, double* diag, int on_device);
 
-/* ------------------------------------------------------------ Davidson a4 */
+/* ------------------------------- Davidson (Sec. II.A, Sec. II.B step 2) */
 /* Lowest eigenpair of H_eff at b.  psi (host, sector-major) is the start
  * vector on entry (NULL = library's current two-site vector or random) and
  * the normalised eigenvector on exit (may be NULL).  Returns
  * GBD_WARN_NOT_CONVERGED if the product limit was reached. */
 int gbd_davidson(gbd_ctx* ctx, int b, double* psi, double* energy, gbd_dav_stats* stats);
 
-/* ------------------------------------------------------------ truncation a5 */
+/* ------------------------------------ truncation (Sec. II.B step 3) */
 /* Truncates the current two-site vector at b to at most Dmax states on the
  * enlarged left (dir = +1) or right (dir = -1) block, renormalises the
- * operators of that block (a6), and forms the next start vector. */
+ * operators of that block (Sec. II.B step 3), and forms the next start
+ * vector ("StVec", Sec. IV). */
 int gbd_truncate(gbd_ctx* ctx, int b, int dir, int Dmax, double* trunc_weight);
 
 /* ------------------------------------------------------------------ sweep */
@@ -256,7 +293,9 @@ int gbd_sweep(gbd_ctx* ctx, int nsweeps, int D, gbd_sweep_stats* stats);
  * current two-site vector (random if none), truncation to D towards dir
  * (+1 right, -1 left), renormalisation, next start vector; with offload on,
  * the next needed environment is loaded and the new one saved to pinned host
- * memory asynchronously (Sec. III.B.4).  The position moves to b + dir. */
+ * memory asynchronously (Sec. III.B.4).  The position moves to b + dir.
+ * Returns GBD_WARN_NOT_CONVERGED (the step still completes) when the
+ * Davidson stopped at its product limit; stats->dav_status says the same. */
 int gbd_step(gbd_ctx* ctx, int b, int dir, int D, gbd_step_stats* stats);
 
 /* Copies the current two-site vector (position *b, sector-major layout) to
@@ -274,7 +313,7 @@ int gbd_launch_count(unsigned long long* count);
 /* Current energies of the last sweep steps, one per step (host array). */
 int gbd_step_energies(gbd_ctx* ctx, double* out, int cap, int* n);
 
-/* ---------------------------------------------------------- pack a7, a8 */
+/* ------------------ serialisation and offload (Sec. III.A, III.B.2-4) */
 /* Environment ids: side 0 = left block (cut c, orbitals 0..c-1), side 1 =
  * right block (cut c, orbitals c..L-1).
  *
@@ -301,8 +340,11 @@ int gbd_unpack_env(gbd_ctx* ctx, int side, int cut, const void* src, size_t byte
 int gbd_env_import(gbd_ctx* ctx, int side, int cut, int ncls, const int* class_meta, int nblk,
                    const int* block_meta, const double* data);
 
-/* Copies a resident environment's arena to host (canonical order, each
- * block padded to an even number of doubles).  *elems gets the arena size. */
+/* Copies an environment's arena to host (canonical order, each block padded
+ * to an even number of doubles).  *elems gets the arena size.  An
+ * environment that lives only in the pinned host store (offload on) is
+ * first loaded back to the device through the offload path (unpack from
+ * pinned memory, package checksums verified: GBD_ERR_CORRUPT on mismatch). */
 int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, size_t* elems);
 
 /* Allocation-free pack.  The paper has no counterpart to this entry point.
@@ -318,11 +360,15 @@ int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, siz
  *
  * arena: device pointer to the environment in the canonical layout of
  * gbd_env_export (blocks class-major, each padded to an even number of
- * doubles); class_meta / block_meta as for gbd_env_import (host memory);
- * side and length are written into every header; dst: device memory of at
- * least the size written to *bytes (too small -> GBD_ERR_ARG with the
- * required size); stream: a cudaStream_t (NULL = legacy default stream); the
- * call returns once the stream has finished the pack.
+ * doubles), at least the padded total of the block sizes long (the library
+ * cannot check that length: a shorter arena is read out of bounds);
+ * class_meta / block_meta as for gbd_env_import (host memory); side and
+ * length are written into every header; dst: device memory of at least the
+ * size written to *bytes (too small -> GBD_ERR_ARG with the required size).
+ * arena and dst must both be 16-byte aligned device (or managed) memory,
+ * else GBD_ERR_ARG before anything is launched.  stream: a cudaStream_t
+ * (NULL = legacy default stream); the call returns once the stream has
+ * finished the pack.
  *
  * Scratch: one file-scope device array of 8 MiB, which every GPU that loads
  * this library holds until the process exits.  Limits: 32768 packages and
@@ -357,8 +403,9 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * and eigensolves, renormalisation, next start vector, IO scheduling, then
  * the enlargement planning (host) in three parts: coefficient links, output
  * blocks, copy and GEMM items, then the algorithmic GB the GBD_MIXED_BF16X3
- * products moved (each operand, X and psi once per product).  *n gets the
- * count; out may be NULL. */
+ * products moved (gbd_heff_info.mixed_bytes per product: operators once,
+ * psi in, H psi out), then their X overhead GB (mixed_x_bytes per product).
+ * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 
 /* Offload statistics of the context so far: bytes saved to / loaded from

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
 HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
 
 FP64, MIXED_BF16X3, SLICED_BF16 = 0, 1, 2
+FAULT_PINNED_ALLOC, FAULT_IO_NEVER_READY, FAULT_CORRUPT_HOST_COPY = 1, 2, 4
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
 WARN_NOT_CONVERGED = 1
@@ -34,7 +35,8 @@ class Config(C.Structure):
                 ("dav_tol", C.c_double), ("dav_max_sub", C.c_int), ("dav_keep", C.c_int),
                 ("dav_max_matvec", C.c_int), ("offload", C.c_int), ("device", C.c_int),
                 ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong),
-                ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int)]
+                ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int), ("fault_inject", C.c_int),
+                ("low_memory", C.c_int)]
 
 
 class SectorInfo(C.Structure):
@@ -44,14 +46,17 @@ class SectorInfo(C.Structure):
 class HeffInfo(C.Structure):
     _fields_ = [("dim", C.c_longlong), ("n_sectors", C.c_int), ("n_terms", C.c_int), ("n_classes", C.c_int),
                 ("n_gemm", C.c_longlong), ("useful_flops", C.c_double), ("operator_bytes", C.c_double),
-                ("mixed_bytes", C.c_double)]
+                ("mixed_bytes", C.c_double), ("mixed_x_bytes", C.c_double), ("mem_operators", C.c_double),
+                ("mem_planes_bf16x3", C.c_double), ("mem_planes_sliced", C.c_double), ("mem_x_fp64", C.c_double),
+                ("mem_x_tensor", C.c_double)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("trunc_weight", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int),
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("ms_davidson", C.c_double),
                 ("ms_truncate", C.c_double), ("ms_renorm", C.c_double), ("ms_io_exposed", C.c_double),
-                ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double)]
+                ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double),
+                ("dav_status", C.c_int)]
 
 
 class DavStats(C.Structure):
@@ -184,8 +189,31 @@ def pack_noalloc(side, length, arena, class_meta, block_meta, dst, stream=None):
     Returns the number of bytes written; raises GbdError (with the required size
     in ``.required``) when dst is too small or a limit is exceeded.
     """
+    # the C side cannot see the arena's length or where the buffers live:
+    # check here, before anything reaches the device
+    for name, t in (("arena", arena), ("dst", dst)):
+        if not (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False)):
+            raise TypeError(f"pack_noalloc: {name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"pack_noalloc: {name} must be contiguous")
+    import torch
+    if arena.dtype != torch.float64:
+        raise TypeError("pack_noalloc: arena must be float64")
+    if dst.dtype != torch.uint8:
+        raise TypeError("pack_noalloc: dst must be uint8")
+    class_meta = np.ascontiguousarray(class_meta, dtype=np.int32).reshape(-1, 3)
+    block_meta = np.ascontiguousarray(block_meta, dtype=np.int32).reshape(-1, 7)
+    need_elems = 0
+    for row in block_meta:
+        ci = int(row[0])
+        if not 0 <= ci < class_meta.shape[0]:
+            raise ValueError("pack_noalloc: block class index out of range")
+        n = int(class_meta[ci, 2]) * int(row[5]) * int(row[6])
+        need_elems += (n + 1) // 2 * 2
+    if arena.numel() < need_elems:
+        raise ValueError(f"pack_noalloc: arena holds {arena.numel()} doubles, the blocks need {need_elems}")
     need = C.c_size_t()
-    nbytes = dst.numel() if hasattr(dst, "numel") else dst.nbytes
+    nbytes = dst.numel()
     rc = lib().gbd_pack_noalloc(side, length, _ptr(arena), class_meta.shape[0], _ptr(class_meta),
                                 block_meta.shape[0], _ptr(block_meta), _ptr(dst), nbytes, C.byref(need),
                                 C.c_void_p(stream))
@@ -201,7 +229,7 @@ class Context:
 
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
-                 mixed_fp64_blocks=False, mixed_polish=2):
+                 mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -209,6 +237,8 @@ class Context:
         cfg.dav_max_sub, cfg.dav_keep, cfg.dav_max_matvec = dav_max_sub, dav_keep, dav_max_matvec
         cfg.switch_cut, cfg.io_timeout_ms, cfg.seed = switch_cut, io_timeout_ms, seed
         cfg.mixed_fp64_blocks, cfg.mixed_polish = int(mixed_fp64_blocks), int(mixed_polish)
+        cfg.fault_inject = int(fault_inject)
+        cfg.low_memory = int(low_memory)
         h = C.c_void_p()
         _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
         self.h = h
@@ -307,6 +337,7 @@ class Context:
         return [s.as_dict() for s in st]
 
     def step(self, b, direction, D):
+        """One two-site iteration; 'dav_status' is 1 when Davidson stopped at its product limit."""
         st = StepStats()
         _check(lib().gbd_step(self.h, b, direction, D, C.byref(st)))
         return {k: getattr(st, k) for k, _ in StepStats._fields_}
@@ -373,7 +404,7 @@ class Context:
               "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop", "renorm_tc_gflop",
               "enlarge_tc_gflop", "step_resident", "step_enlarge", "step_davidson", "step_rho_eig", "step_renorm",
               "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
-              "products_bf16x3_gbytes"]
+              "products_bf16x3_gbytes", "products_bf16x3_x_gbytes"]
 
     def timers(self):
         out = np.zeros(64)

@@ -63,6 +63,8 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->seed = 12345;
     cfg->mixed_fp64_blocks = 0;
     cfg->mixed_polish = 2;
+    cfg->fault_inject = 0;
+    cfg->low_memory = 0;
     return GBD_OK;
 }
 
@@ -79,6 +81,7 @@ int gbd_create(const gbd_config* cfg, gbd_ctx** out) {
                         cfg->dav_max_matvec >= 1 && cfg->dav_tol > 0 && cfg->io_timeout_ms > 0,
                     GBD_ERR_ARG, "bad solver settings");
         GBD_REQUIRE(cfg->mixed_polish >= 0 && cfg->mixed_polish <= 2, GBD_ERR_ARG, "mixed_polish must be 0, 1 or 2");
+        GBD_REQUIRE(cfg->low_memory >= -1 && cfg->low_memory <= 1, GBD_ERR_ARG, "low_memory must be -1, 0 or 1");
         auto* c = new gbd_ctx();
         c->C.cfg = *cfg;
         *out = c;
@@ -192,6 +195,12 @@ int gbd_build_tables(gbd_ctx* c, int b, gbd_sector_info* out, int cap, int* n, g
             info->useful_flops = H.flops;
             info->operator_bytes = H.op_bytes;
             info->mixed_bytes = H.mixed_bytes;
+            info->mixed_x_bytes = H.mixed_x_bytes;
+            info->mem_operators = H.mem_ops;
+            info->mem_planes_bf16x3 = H.mem_bf16x3;
+            info->mem_planes_sliced = H.mem_sliced;
+            info->mem_x_fp64 = H.mem_x64;
+            info->mem_x_tensor = H.mem_xtc;
         }
         return GBD_OK;
     });
@@ -261,8 +270,7 @@ int gbd_step(gbd_ctx* c, int b, int dir, int D, gbd_step_stats* stats) {
     return guard([&] {
         GBD_REQUIRE(dir == 1 || dir == -1, GBD_ERR_ARG, "dir must be +1 or -1");
         GBD_REQUIRE(D >= 1, GBD_ERR_ARG, "D must be >= 1");
-        run_step(ctx(c), b, dir, D, stats);
-        return GBD_OK;
+        return run_step(ctx(c), b, dir, D, stats);
     });
 }
 
@@ -410,7 +418,8 @@ int gbd_env_export(gbd_ctx* c, int side, int cut, double* out, size_t cap, size_
     return guard([&] {
         Ctx& C = ctx(c);
         OpSet* E = env_of(C, side, cut, false);
-        GBD_REQUIRE(E && E->resident(), GBD_ERR_STATE, "environment not resident");
+        GBD_REQUIRE(E, GBD_ERR_STATE, "environment never built");
+        if (!E->resident()) make_resident(C, side, cut);
         if (elems) *elems = size_t(E->total);
         GBD_REQUIRE(out && cap >= size_t(E->total), GBD_ERR_ARG, "output too small");
         GBD_CHECK_CUDA(cudaMemcpy(out, E->data.p, size_t(E->total) * sizeof(double), cudaMemcpyDeviceToHost));

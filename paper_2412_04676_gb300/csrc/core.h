@@ -138,6 +138,7 @@ struct OpClass {
 void* devcache_get(size_t n, cudaStream_t st, size_t* got);
 void devcache_put(void* p, size_t bytes, cudaStream_t st);  // never throws
 void devcache_trim();                                        // cudaFree every cached block
+size_t devcache_bytes();                                     // bytes held in cached blocks
 
 struct DevBuf {
     void* p = nullptr;

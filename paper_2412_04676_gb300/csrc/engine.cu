@@ -13,7 +13,8 @@
 //
 // Every block product runs through one grouped-GEMM launch per phase (FP64
 // engine in kernels.cu, BF16x3 tensor-core engine in tc.cu); the host builds
-// the task tables from the sector tables (row a1) and the MPO (row a2).
+// the task tables from the sector tables (Fig. 4a) and the operator sets of
+// Eq. 1 split at every cut (mpo.cpp).
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
@@ -419,6 +420,20 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
 }
 
 // ============================================================== renormalisation
+// useful flops of the two renormalisation GEMM phases (2 M N K each)
+static double renorm_flops(const OpSet& O, const Iso& U, const OpSet& out) {
+    (void)O;
+    double f = 0.0;
+    for (size_t c = 0; c < out.cls.size(); ++c) {
+        const double T = double(out.cls[c].states.size());
+        for (const auto& nb : out.cls[c].blocks) {
+            const double dimO = U.basis.dim[U.basis.find(nb.Qo)], dimI = U.basis.dim[U.basis.find(nb.Qi)];
+            f += 2.0 * T * dimO * nb.cols * dimI + 2.0 * T * nb.rows * nb.cols * dimO;
+        }
+    }
+    return f;
+}
+
 // Post-processing (Sec. II.B step 3): E_new[t] = U_Q^T O[t] U_Q2 for every
 // block of the enlarged operator set whose two sectors are kept.
 static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
@@ -454,74 +469,78 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
         }
     C.scratch_tmp.ensure(size_t(std::max<long long>(tmp_tot, 1)) * sizeof(double));
     double* tmp = C.scratch_tmp.as<double>();
-    const double* dO = O.data.as<double>();
-    const double* dU = U.data.as<double>();
-    double* dN = out.data.as<double>();
-    GemmPlan& PA = C.plan_a;
-    GemmPlan& PB = C.plan_b;
-    PA.clear();
-    PB.clear();
-    size_t j = 0;
-    for (size_t c = 0; c < out.cls.size(); ++c) {
-        int T = int(out.cls[c].states.size());
-        for (const auto& nb : out.cls[c].blocks) {
-            int eo = U.basis.find(nb.Qo), ei = U.basis.find(nb.Qi);
-            int dimO = U.basis.dim[eo], dimI = U.basis.dim[ei];
-            int bi = -1;
-            for (size_t x = 0; x < O.cls[c].blocks.size(); ++x)
-                if (O.cls[c].blocks[x].qo == eo && O.cls[c].blocks[x].qi == ei) bi = int(x);
-            GBD_REQUIRE(bi >= 0, GBD_ERR_STATE, "renormalisation: missing enlarged block");
-            const OpBlock& ob = O.cls[c].blocks[bi];
-            GemmTask ta{};
-            ta.C = tmp + toff[j];
-            ta.ldc = nb.cols;
-            ta.M = T * dimO;
-            ta.N = nb.cols;
-            ta.nbatch = 1;
-            GemmSeg ga{};
-            ga.A = dO + ob.off;
-            ga.lda = dimI;
-            ga.B = dU + U.off[nb.qi];
-            ga.ldb = nb.cols;
-            ga.K = dimI;
-            ga.T = 1;
-            ga.coef = 1.0;
-            PA.add_task(ta, {ga});
-            GemmTask tb{};
-            tb.C = dN + nb.off;
-            tb.ldc = nb.cols;
-            tb.M = nb.rows;
-            tb.N = nb.cols;
-            tb.nbatch = T;
-            tb.bC = (long long)nb.rows * nb.cols;
-            tb.bB = (long long)dimO * nb.cols;
-            tb.bA = 0;
-            GemmSeg gb{};
-            gb.A = dU + U.off[nb.qo];
-            gb.lda = nb.rows;
-            gb.transA = 1;
-            gb.B = tmp + toff[j];
-            gb.ldb = nb.cols;
-            gb.K = dimO;
-            gb.T = 1;
-            gb.coef = 1.0;
-            PB.add_task(tb, {gb});
-            ++j;
-        }
-    }
-    std::vector<std::pair<const void*, size_t>> bufs = {{O.data.p, size_t(O.total) * 8},
-                                                        {U.data.p, U.data.bytes},
-                                                        {C.scratch_tmp.p, C.scratch_tmp.bytes},
-                                                        {out.data.p, size_t(out.total) * 8}};
-    PA.check(bufs, "renormalise/A");
-    PB.check(bufs, "renormalise/B");
-    const double t_dev0 = wall_ms();
-    C.timers[Ctx::T_REN_HOST] += t_dev0 - t_host0;
     // mixed form: both GEMM phases on the tensor cores in the sliced form when
     // the enlarged set's slices exist (FP64 GEMMs otherwise)
+    double t_dev0 = wall_ms();
+    C.timers[Ctx::T_REN_HOST] += t_dev0 - t_host0;
     if (C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2 && tc_renormalize(C, O, U, out, toff, tmp)) {
-        C.timers[Ctx::T_REN_TC_GFLOP] += (PA.flops + PB.flops) * 1e-9;
+        C.timers[Ctx::T_REN_TC_GFLOP] += renorm_flops(O, U, out) * 1e-9;
     } else {
+        GBD_REQUIRE(O.resident(), GBD_ERR_STATE, "renormalisation: enlarged operators released and no sliced planes");
+        const double t_plan0 = wall_ms();
+        const double* dO = O.data.as<double>();
+        const double* dU = U.data.as<double>();
+        double* dN = out.data.as<double>();
+        GemmPlan& PA = C.plan_a;
+        GemmPlan& PB = C.plan_b;
+        PA.clear();
+        PB.clear();
+        size_t j = 0;
+        for (size_t c = 0; c < out.cls.size(); ++c) {
+            int T = int(out.cls[c].states.size());
+            for (const auto& nb : out.cls[c].blocks) {
+                int eo = U.basis.find(nb.Qo), ei = U.basis.find(nb.Qi);
+                int dimO = U.basis.dim[eo], dimI = U.basis.dim[ei];
+                int bi = -1;
+                for (size_t x = 0; x < O.cls[c].blocks.size(); ++x)
+                    if (O.cls[c].blocks[x].qo == eo && O.cls[c].blocks[x].qi == ei) bi = int(x);
+                GBD_REQUIRE(bi >= 0, GBD_ERR_STATE, "renormalisation: missing enlarged block");
+                const OpBlock& ob = O.cls[c].blocks[bi];
+                GemmTask ta{};
+                ta.C = tmp + toff[j];
+                ta.ldc = nb.cols;
+                ta.M = T * dimO;
+                ta.N = nb.cols;
+                ta.nbatch = 1;
+                GemmSeg ga{};
+                ga.A = dO + ob.off;
+                ga.lda = dimI;
+                ga.B = dU + U.off[nb.qi];
+                ga.ldb = nb.cols;
+                ga.K = dimI;
+                ga.T = 1;
+                ga.coef = 1.0;
+                PA.add_task(ta, {ga});
+                GemmTask tb{};
+                tb.C = dN + nb.off;
+                tb.ldc = nb.cols;
+                tb.M = nb.rows;
+                tb.N = nb.cols;
+                tb.nbatch = T;
+                tb.bC = (long long)nb.rows * nb.cols;
+                tb.bB = (long long)dimO * nb.cols;
+                tb.bA = 0;
+                GemmSeg gb{};
+                gb.A = dU + U.off[nb.qo];
+                gb.lda = nb.rows;
+                gb.transA = 1;
+                gb.B = tmp + toff[j];
+                gb.ldb = nb.cols;
+                gb.K = dimO;
+                gb.T = 1;
+                gb.coef = 1.0;
+                PB.add_task(tb, {gb});
+                ++j;
+            }
+        }
+        std::vector<std::pair<const void*, size_t>> bufs = {{O.data.p, size_t(O.total) * 8},
+                                                            {U.data.p, U.data.bytes},
+                                                            {C.scratch_tmp.p, C.scratch_tmp.bytes},
+                                                            {out.data.p, size_t(out.total) * 8}};
+        PA.check(bufs, "renormalise/A");
+        PB.check(bufs, "renormalise/B");
+        C.timers[Ctx::T_REN_HOST] += wall_ms() - t_plan0;
+        t_dev0 = wall_ms();
         C.timers[Ctx::T_REN_GFLOP] += (PA.flops + PB.flops) * 1e-9;
         PA.upload(C.cs);
         PA.launch(C.cs);
@@ -791,6 +810,10 @@ void build_envs(Ctx& C, int b) {
     for (int k = 0; k < b; ++k) GBD_REQUIRE(C.site_kind[k] == 0, GBD_ERR_ARG, "sites left of b must be left-isometric");
     for (int k = b + 2; k < C.L; ++k)
         GBD_REQUIRE(C.site_kind[k] == 1, GBD_ERR_ARG, "sites right of b+1 must be right-isometric");
+    // with offload on, every environment the position b does not use goes to
+    // the pinned host store as soon as the next one is built from it, so the
+    // device holds two or three environments at a time
+    const bool off = C.cfg.offload != 0;
     C.envL[0] = trivial_env(C, 0);
     for (int k = 0; k < b; ++k) {
         OpSet O;
@@ -799,6 +822,7 @@ void build_envs(Ctx& C, int b) {
         auto E = std::make_unique<OpSet>();
         renormalize(C, O, C.sites[k], *E);
         C.envL[k + 1] = std::move(E);
+        if (off) offload_env(C, 0, k);
     }
     C.envR[C.L] = trivial_env(C, 1);
     for (int k = C.L - 1; k >= b + 2; --k) {
@@ -808,6 +832,7 @@ void build_envs(Ctx& C, int b) {
         auto E = std::make_unique<OpSet>();
         renormalize(C, O, C.sites[k], *E);
         C.envR[k] = std::move(E);
+        if (off) offload_env(C, 1, k + 1);
     }
     C.H = Heff();
     C.psi_valid = false;
@@ -871,11 +896,24 @@ void setup_heff(Ctx& C, int b) {
     }
     H.xtot = xtot;
     {
-        double elems = 0.0;
+        // algorithmic bytes of one BF16x3 product: each operator element read
+        // once (hi + lo), psi in and H psi out; the X round trip is overhead
+        double elems = 0.0, padded = 0.0, xpad = 0.0;
         for (const OpSet* O : {&H.OL, &H.OR})
             for (const auto& c : O->cls)
-                for (const auto& bb : c.blocks) elems += double(c.states.size()) * bb.rows * bb.cols;
-        H.mixed_bytes = 4.0 * elems + 8.0 * nx + 16.0 * double(H.dim);
+                for (const auto& bb : c.blocks) {
+                    elems += double(c.states.size()) * bb.rows * bb.cols;
+                    padded += double(c.states.size()) * bb.rows * ((bb.cols + 7) / 8 * 8);
+                }
+        for (const auto& p : H.pairs)
+            xpad += double(H.OL.cls[p.c].states.size()) * H.bL.dim[H.sL[p.s_out]] * ((H.bR.dim[H.sR[p.s_in]] + 7) / 8 * 8);
+        H.mixed_bytes = 4.0 * elems + 16.0 * double(H.dim);
+        H.mixed_x_bytes = 8.0 * nx;
+        H.mem_ops = H.op_bytes;
+        H.mem_bf16x3 = 4.0 * padded;
+        H.mem_sliced = 8.0 * padded;
+        H.mem_x64 = 8.0 * double(xtot);
+        H.mem_xtc = 8.0 * xpad;
     }
     H.fp64_ready = false;
     H.diag_ready = false;
@@ -955,6 +993,9 @@ void build_fp64_plans(Ctx& C) {
 
 
 void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
+    // an FP64 product after the mixed form released the FP64 enlarged
+    // operators (low-memory mode) enlarges them again
+    if (precision == GBD_FP64 && !(C.H.OL.resident() && C.H.OR.resident())) setup_heff(C, C.H.b);
     Heff& H = C.H;
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
@@ -990,10 +1031,14 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     C.timers[Ctx::T_PROD_MS0 + precision] += ms;
     C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
     C.timers[Ctx::T_PROD_GF0 + precision] += H.flops * 1e-9;
-    if (precision == GBD_MIXED_BF16X3) C.timers[Ctx::T_PROD_GB1] += H.mixed_bytes * 1e-9;
+    if (precision == GBD_MIXED_BF16X3) {
+        C.timers[Ctx::T_PROD_GB1] += H.mixed_bytes * 1e-9;
+        C.timers[Ctx::T_PROD_XGB1] += H.mixed_x_bytes * 1e-9;
+    }
 }
 
 void heff_diag(Ctx& C) {
+    if (!C.H.diag_ready && !(C.H.OL.resident() && C.H.OR.resident())) setup_heff(C, C.H.b);
     Heff& H = C.H;
     if (H.diag_ready) return;
     std::vector<DiagTask> tasks;
@@ -1514,7 +1559,10 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     P.check({{C.psi.p, C.psi.bytes}, {I.data.p, I.data.bytes}, {Cbuf.p, Cbuf.bytes}}, "truncate/C");
     P.upload(s);
     P.launch(s);
-    // renormalised environment of the truncated block (row a6)
+    // the position's products are done: only the sliced operator planes (read
+    // by the renormalisation) stay on the device
+    if (H.tc_ready) tc_release_products(C);
+    // renormalised environment of the truncated block (Sec. II.B step 3)
     auto E = std::make_unique<OpSet>();
     if (!C.marks.empty()) step_mark(C, Ctx::T_PH_RENORM);
     if (dir == 1) renormalize(C, H.OL, I, *E);

@@ -62,7 +62,10 @@ struct Heff {
     DevBuf X, xin, yout, diag;
     bool diag_ready = false;
     long long ngemm = 0;
-    double flops = 0.0, op_bytes = 0.0, mixed_bytes = 0.0;
+    double flops = 0.0, op_bytes = 0.0, mixed_bytes = 0.0, mixed_x_bytes = 0.0;
+    // device memory model (bytes): enlarged FP64 arenas, tensor-core operator
+    // planes of each form, phase-1 intermediates
+    double mem_ops = 0.0, mem_bf16x3 = 0.0, mem_sliced = 0.0, mem_x64 = 0.0, mem_xtc = 0.0;
     TcHeff tc;               // mixed-precision (BF16x3, tcgen05) operands and plans
     bool tc_ready = false;
     int sector_of(const Q& q) const {
@@ -118,7 +121,7 @@ struct Ctx {
            T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
            // device time of the phases of gbd_step on the compute stream (host gaps included)
            T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
-           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_COUNT };
+           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};
@@ -140,8 +143,10 @@ void heff_diag(Ctx& C);
 int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st);
 double truncate_step(Ctx& C, int dir, int Dmax);
 int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* st);
-void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* st);
+int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* st);  // GBD_OK or GBD_WARN_NOT_CONVERGED
 void collect_saves(Ctx& C, bool wait);
+void make_resident(Ctx& C, int side, int cut);  // loads an offloaded environment back (checksums verified)
+void offload_env(Ctx& C, int side, int cut);    // asynchronous save to pinned host memory, then device release
 
 // pack / unpack (serialisation)
 size_t pack_size(const OpSet& E);

@@ -576,6 +576,11 @@ void devcache_put(void* p, size_t bytes, cudaStream_t st) {
     }
 }
 
+size_t devcache_bytes() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    return g_cache_bytes;
+}
+
 void devcache_trim() {
     std::vector<CacheBlock> all;
     {

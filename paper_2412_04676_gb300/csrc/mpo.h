@@ -1,4 +1,5 @@
-// mpo.h -- left/right operator sets of Eq. 1 at every cut (host tables, row a2).
+// mpo.h -- left/right operator sets of Eq. 1 at every cut (host tables; the term
+// split of Sec. II.B step 1).
 #pragma once
 
 #include <cstdint>

@@ -96,6 +96,20 @@ extern "C" int gbd_pack_noalloc(int side, int length, const double* arena, int n
         GBD_REQUIRE(dst && cap >= total, GBD_ERR_ARG, "destination too small (required size written to *bytes)");
         GBD_REQUIRE(nblk == 0 || arena, GBD_ERR_ARG, "null arena");
         if (nblk == 0) return GBD_OK;
+        // the kernels move 16-byte vectors and run on the device: both
+        // buffers must be 16-byte aligned memory the device can address
+        GBD_REQUIRE((reinterpret_cast<uintptr_t>(arena) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0,
+                    GBD_ERR_ARG, "arena and dst must be 16-byte aligned");
+        for (const void* p : {static_cast<const void*>(arena), static_cast<const void*>(dst)}) {
+            cudaPointerAttributes at{};
+            const cudaError_t r = cudaPointerGetAttributes(&at, p);
+            if (r != cudaSuccess) {
+                cudaGetLastError();
+                throw Error(GBD_ERR_ARG, "arena and dst must be device memory");
+            }
+            GBD_REQUIRE(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged, GBD_ERR_ARG,
+                        "arena and dst must be device memory");
+        }
         // headers and tables on the host, copied into the file-scope scratch
         std::vector<unsigned char> hdr(size_t(nblk) * 64, 0);
         std::vector<PackItem> items(nblk);

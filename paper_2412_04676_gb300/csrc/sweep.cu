@@ -248,8 +248,9 @@ double now_ms() {
 void wait_event(Ctx& C, cudaEvent_t e) {
     if (!e) return;
     double t0 = now_ms();
+    const bool never = (C.cfg.fault_inject & GBD_FAULT_IO_NEVER_READY) != 0;
     while (true) {
-        cudaError_t r = cudaEventQuery(e);
+        cudaError_t r = never ? cudaErrorNotReady : cudaEventQuery(e);
         if (r == cudaSuccess) break;
         if (r != cudaErrorNotReady) GBD_CHECK_CUDA(r);
         if (now_ms() - t0 > C.cfg.io_timeout_ms) throw Error(GBD_ERR_TIMEOUT, "IO event wait timed out");
@@ -260,12 +261,14 @@ void wait_event(Ctx& C, cudaEvent_t e) {
 
 HostEnv& host_of(Ctx& C, int side, int cut) { return side == 0 ? C.hostL[cut] : C.hostR[cut]; }
 
-void pinned_grow(unsigned char*& p, size_t& cap, size_t need) {
+void pinned_grow(const Ctx& C, unsigned char*& p, size_t& cap, size_t need) {
     if (need <= cap && p) return;
     if (p) cudaFreeHost(p);
     p = nullptr;
     size_t c = std::max(need, cap + cap / 4);
-    if (cudaHostAlloc((void**)&p, c, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    if ((C.cfg.fault_inject & GBD_FAULT_PINNED_ALLOC) ||
+        cudaHostAlloc((void**)&p, c, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
         p = nullptr;
         cap = 0;
         throw Error(GBD_ERR_HOST_OOM, "pinned host allocation failed");
@@ -280,10 +283,10 @@ template <class T> T* dev_view(void* host) {
 }
 
 // item + chunk tables copied into the id's mapped pinned buffer
-void stage_tables(HostEnv& h, const PackHost& P, PackItem** d_items, PackChunk** d_chunks) {
+void stage_tables(const Ctx& C, HostEnv& h, const PackHost& P, PackItem** d_items, PackChunk** d_chunks) {
     size_t ib = P.items.size() * sizeof(PackItem), cb = P.chunks.size() * sizeof(PackChunk);
     size_t ib16 = pad16(ib);
-    pinned_grow(h.meta, h.meta_cap, ib16 + cb + 16);
+    pinned_grow(C, h.meta, h.meta_cap, ib16 + cb + 16);
     if (ib) std::memcpy(h.meta, P.items.data(), ib);
     if (cb) std::memcpy(h.meta + ib16, P.chunks.data(), cb);
     unsigned char* d = dev_view<unsigned char>(h.meta);
@@ -312,14 +315,14 @@ void save_async(Ctx& C, int side, int cut) {
     if (h.pending) wait_event(C, h.loaded);
     PackHost P;
     build_pack(C, *E, P);
-    pinned_grow(h.host, h.cap, std::max<size_t>(P.total, 64));
+    pinned_grow(C, h.host, h.cap, std::max<size_t>(P.total, 64));
     if (!h.done) GBD_CHECK_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
     h.bytes = P.total;
     h.npk = int(P.items.size());
     for (size_t i = 0; i < P.items.size(); ++i) std::memcpy(h.host + P.items[i].pkg, P.headers.data() + i * 64, 64);
     PackItem* di = nullptr;
     PackChunk* dc = nullptr;
-    stage_tables(h, P, &di, &dc);
+    stage_tables(C, h, P, &di, &dc);
     cudaEvent_t ready;
     GBD_CHECK_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     GBD_CHECK_CUDA(cudaEventRecord(ready, C.cs));
@@ -387,9 +390,15 @@ void load_async(Ctx& C, int side, int cut) {
         off += 64 + pad16(pb);
     }
     h.want.resize(P.items.size());
+    if (C.cfg.fault_inject & GBD_FAULT_CORRUPT_HOST_COPY) {
+        // one payload byte of the first non-empty package is flipped in host
+        // memory after its save finished: the checksum must catch it
+        for (const auto& it : P.items)
+            if (it.words > 0) { h.host[it.pkg + 64] ^= 0x01; break; }
+    }
     PackItem* di = nullptr;
     PackChunk* dc = nullptr;
-    stage_tables(h, P, &di, &dc);
+    stage_tables(C, h, P, &di, &dc);
     GBD_CHECK_CUDA(cudaMemsetAsync(h.cks_dev, 0, std::max<size_t>(P.items.size(), 1) * 8, C.ios));
     unpack_launch(dev_view<unsigned char>(h.host), di, dc, int(P.chunks.size()), h.cks_dev, C.ios);
     if (!P.items.empty())
@@ -415,6 +424,21 @@ void ensure_resident(Ctx& C, int side, int cut) {
 
 }  // namespace
 
+// Saves an environment to the pinned host store and releases its device
+// arena once the save and every use already enqueued have finished.
+void offload_env(Ctx& C, int side, int cut) {
+    save_async(C, side, cut);
+    release_async(C, side, cut);
+}
+
+// An environment made resident for the caller: if it lives only in the
+// pinned host store it is loaded back through the offload path (unpack from
+// mapped pinned memory, checksums verified).
+void make_resident(Ctx& C, int side, int cut) {
+    ensure_cuda(C);
+    ensure_resident(C, side, cut);
+}
+
 // collect the device time of finished asynchronous saves
 void collect_saves(Ctx& C, bool wait) {
     std::vector<Ctx::PendingSave> keep;
@@ -435,7 +459,7 @@ void collect_saves(Ctx& C, bool wait) {
 
 // ============================================================== step / sweep
 // One DMRG iteration of Sec. II.B at position b, moving towards dir.
-void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
+int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     GBD_REQUIRE(C.have_ints, GBD_ERR_STATE, "load integrals first");
     GBD_REQUIRE(b >= 0 && b + 1 < C.L, GBD_ERR_ARG, "two-site position out of range");
     ensure_cuda(C);
@@ -463,7 +487,7 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     double e = 0.0;
     gbd_dav_stats ds{};
     step_mark(C, Ctx::T_PH_DAVIDSON);
-    davidson(C, nullptr, &e, &ds);
+    const int dav_status = davidson(C, nullptr, &e, &ds);
     double flops = C.H.flops * ds.matvecs;
     double t2 = now_ms();
     double w = truncate_step(C, dir, D);
@@ -505,7 +529,9 @@ void run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
         out->ms_io_exposed = C.io_exposed_ms - io0;
         out->useful_flops = flops;
         out->bytes_packed = C.io_d2h - d2h0;
+        out->dav_status = dav_status;
     }
+    return dav_status;
 }
 
 int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* stats) {

@@ -140,6 +140,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// OR of a flag over the epilogue warps (named barrier 1, the barrier of the
+// staging planes): every epilogue warp gets the same answer
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred q, p;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(uint32_t(v)), "n"(EPI_THREADS)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ int vload(const int& x) { return *reinterpret_cast<const volatile int*>(&x); }
+__device__ __forceinline__ void vstore(int& x, int v) { *reinterpret_cast<volatile int*>(&x) = v; }
+
 // MMA width of a work item: its valid columns rounded up to 16, at most BN
 template <int BN_> __device__ __forceinline__ int tile_n_of(int N, int n0) {
     const int v = N - n0;
@@ -211,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         long long g = 0;  // chunks issued by this CTA
-        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+        for (int wi = blockIdx.x; wi < nworks && !vload(abort_s); wi += gridDim.x) {
             const Work w = works[wi];
             const int n = w.c1 - w.c0;
             if (n <= 0) continue;
@@ -221,10 +236,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int st = int(g % K_::ST);
                 if (g >= K_::ST && !mbar_wait(smem_u32(&empty_bar[st]), uint32_t(((g / K_::ST) & 1) ^ 1))) {
                     atomicExch(err, 1);
-                    abort_s = 1;
+                    vstore(abort_s, 1);
                     break;
                 }
-                if (abort_s) break;
+                if (vload(abort_s)) break;
                 const KSeg sg = segs[s];
                 const uint32_t bar = smem_u32(&full_bar[st]);
                 uint8_t* base = smem + st * K_::STAGE_BYTES;
@@ -252,14 +267,14 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             }
         }
         // on abort: let the loads already issued land before the CTA may exit
-        if (abort_s)
+        if (vload(abort_s))
             for (long long i = (g > K_::ST ? g - K_::ST : 0); i < g; ++i)
                 mbar_wait(smem_u32(&full_bar[i % K_::ST]), uint32_t((i / K_::ST) & 1));
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         long long g = 0;   // chunks consumed
         int D = 0;         // accumulator fills started (buffer D & 1)
-        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+        for (int wi = blockIdx.x; wi < nworks && !vload(abort_s); wi += gridDim.x) {
             const Work w = works[wi];
             const int n = w.c1 - w.c0;
             if (n <= 0) continue;
@@ -271,16 +286,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int st = int(g % K_::ST);
                 if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / K_::ST) & 1))) {
                     atomicExch(err, 2);
-                    abort_s = 1;
+                    vstore(abort_s, 1);
                     break;
                 }
-                if (abort_s) break;
+                if (vload(abort_s)) break;
                 tc_fence_after();
                 const int buf = D & 1;
                 if (inbuf == 0 && (D >> 1) > 0) {
                     if (!mbar_wait(smem_u32(&tempty[buf]), uint32_t(((D >> 1) - 1) & 1))) {
                         atomicExch(err, 3);
-                        abort_s = 1;
+                        vstore(abort_s, 1);
                         break;
                     }
                     tc_fence_after();
@@ -337,7 +352,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
         const int part = (warp - 2) >> 2;   // column slice of CP columns
         const int row = quad * 32 + lane;
         int D = 0;
-        for (int wi = blockIdx.x; wi < nworks && !abort_s; wi += gridDim.x) {
+        // Phase 1 stages its output through named barrier 1, so its epilogue
+        // warps leave the item loop only together: the loop does not test
+        // the abort flag, and after each item's drains every epilogue warp,
+        // one that gave up on a wait included, votes before the staging
+        // barriers.  The other phases use no named barrier and leave alone.
+        for (int wi = blockIdx.x; wi < nworks && (PH == 1 || !vload(abort_s)); wi += gridDim.x) {
             int ndrain, nn;
             {
                 const int n = works[wi].c1 - works[wi].c0;
@@ -348,9 +368,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             float ah[CP], al[CP];
 #pragma unroll
             for (int i = 0; i < CP; ++i) { ah[i] = 0.f; al[i] = 0.f; }
+            bool gave_up = false;
             for (int dd = 0; dd < ndrain; ++dd, ++D) {
                 const int buf = D & 1;
-                if (!mbar_wait(smem_u32(&tfull[buf]), uint32_t((D >> 1) & 1))) { atomicExch(err, 4); abort_s = 1; break; }
+                // warp-uniform outcome: the TMEM loads below are .sync.aligned
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[buf]), uint32_t((D >> 1) & 1)))) {
+                    if (lane == 0) atomicExch(err, 4);
+                    vstore(abort_s, 1);
+                    gave_up = true;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t tb = tmem + (uint32_t(quad * 32) << 16) + uint32_t(buf * K_::BUFCOLS + part * CP);
                 if constexpr (MODE == 0) {
@@ -385,7 +412,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
             }
-            if (abort_s) break;
+            if constexpr (PH == 1) {
+                if (epi_any(gave_up || vload(abort_s))) break;
+            } else {
+                if (gave_up || vload(abort_s)) break;
+            }
             const Work w = works[wi];  // loaded after the drains: keeps registers free for ah / al
             if constexpr (PH == 3) {
                 const int gr = w.m0 + row;
@@ -839,6 +870,53 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
     T.blk_b.upload(st);
 }
 
+// Operator slice planes of one product form for one side (0: O^Lx, 1:
+// O^xR), split from the FP64 enlarged arena of that side.
+template <int MODE> void build_ops(Ctx& C, int side) {
+    constexpr int NS = ModeCfg<MODE>::NS;
+    Heff& H = C.H;
+    TcPlan& P = H.tc.pl[MODE];
+    cudaStream_t st = C.cs;
+    const OpSet& O = side == 0 ? H.OL : H.OR;
+    GBD_REQUIRE(O.resident(), GBD_ERR_STATE, "enlarged operators not resident for the operator planes");
+    std::vector<std::vector<long long>> off;
+    const long long n = std::max(op_layout(O, off), 8LL);
+    DevBuf& dst = side == 0 ? P.ol : P.orr;
+    (side == 0 ? P.nL : P.nR) = n;
+    dst.ensure_cached(size_t(n) * NS * 2, st);
+    // concat: layers side by side along each row ([row][layer][col]), the
+    // BF16x3 phase-2 B operand; otherwise layer-stacked rows
+    const bool concat = MODE == 0 && side == 1;
+    std::vector<SplitDesc> sd;
+    for (size_t c = 0; c < O.cls.size(); ++c)
+        for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
+            const OpBlock& b = O.cls[c].blocks[i];
+            const long long Tn = (long long)O.cls[c].states.size();
+            const long long rows = Tn * b.rows;
+            const int ldd = pad8(b.cols);
+            const long long per = std::max<long long>(1, kSplitUnits / ((ldd + 63) / 64));
+            for (long long r0 = 0; r0 < rows; r0 += per) {
+                SplitDesc q{O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
+                            b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i], n, 1LL << 62, 0, ldd, r0};
+                if (concat) { q.R = std::max(b.rows, 1); q.lpitch = ldd; q.rpitch = Tn * ldd; }
+                sd.push_back(q);
+            }
+        }
+    if (!sd.empty()) {
+        DevBuf d;
+        upload_vec(d, sd, st);
+        for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
+            const unsigned nb = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
+            split_kernel<MODE><<<nb, 256, 0, st>>>(d.as<SplitDesc>() + i0);
+            count_launch();
+        }
+        GBD_CHECK_CUDA(cudaGetLastError());
+        GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffer is freed on return
+    }
+    P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
+    (side == 0 ? P.ops_l : P.ops_r) = true;
+}
+
 // Slice planes, tensor maps and work lists of one product form.
 template <int MODE> void build_plan(Ctx& C) {
     constexpr int NS = ModeCfg<MODE>::NS, TBN = ModeCfg<MODE>::BN;
@@ -847,48 +925,12 @@ template <int MODE> void build_plan(Ctx& C) {
     TcPlan& P = T.pl[MODE];
     cudaStream_t st = C.cs;
     const double t0 = wall_ms();
-    // ---- operator slice planes
+    // ---- operator slice planes (already built when the FP64 arenas were released)
+    if (!P.ops_l) build_ops<MODE>(C, 0);
+    if (!P.ops_r) build_ops<MODE>(C, 1);
     std::vector<std::vector<long long>> offL, offR;
-    P.nL = std::max(op_layout(H.OL, offL), 8LL);
-    P.nR = std::max(op_layout(H.OR, offR), 8LL);
-    P.ol.ensure_cached(size_t(P.nL) * NS * 2, st);
-    P.orr.ensure_cached(size_t(P.nR) * NS * 2, st);
-    P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
-    {
-        DevBuf d;
-        std::vector<SplitDesc> sd;
-        // concat: layers side by side along each row ([row][layer][col]), the
-        // BF16x3 phase-2 B operand; otherwise layer-stacked rows
-        auto add = [&](const OpSet& O, const std::vector<std::vector<long long>>& off, DevBuf& dst, long long plane,
-                       bool concat) {
-            for (size_t c = 0; c < O.cls.size(); ++c)
-                for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
-                    const OpBlock& b = O.cls[c].blocks[i];
-                    const long long Tn = (long long)O.cls[c].states.size();
-                    const long long rows = Tn * b.rows;
-                    const int ldd = pad8(b.cols);
-                    const long long per = std::max<long long>(1, kSplitUnits / ((ldd + 63) / 64));
-                    for (long long r0 = 0; r0 < rows; r0 += per) {
-                        SplitDesc q{O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
-                                    b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i], plane, 1LL << 62, 0, ldd, r0};
-                        if (concat) { q.R = std::max(b.rows, 1); q.lpitch = ldd; q.rpitch = Tn * ldd; }
-                        sd.push_back(q);
-                    }
-                }
-        };
-        add(H.OL, offL, P.ol, P.nL, false);
-        add(H.OR, offR, P.orr, P.nR, MODE == 0);
-        if (!sd.empty()) {
-            upload_vec(d, sd, st);
-            for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
-                const unsigned n = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
-                split_kernel<MODE><<<n, 256, 0, st>>>(d.as<SplitDesc>() + i0);
-                count_launch();
-            }
-            GBD_CHECK_CUDA(cudaGetLastError());
-            GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffer is freed on return
-        }
-    }
+    op_layout(H.OL, offL);
+    op_layout(H.OR, offR);
     const double t1 = wall_ms();
     if (MODE == 0) build_block_terms(C, P, offL, offR);
     // ---- psi^T slice planes
@@ -923,7 +965,10 @@ template <int MODE> void build_plan(Ctx& C) {
         return H.bL.dim[H.sL[a.si]] > H.bL.dim[H.sL[b.si]];
     });
     P.nx = std::max(nx, 8LL);
-    P.x.ensure_cached(size_t(P.nx) * NS * 2, st);
+    // one phase-1 buffer serves both forms (they never run at the same time):
+    // sized for the four slice planes of the sliced form
+    T.x.ensure_cached(size_t(P.nx) * ModeCfg<1>::NS * 2, st);
+    __nv_bfloat16* const xbase = T.x.as<__nv_bfloat16>();
     // ---- tensor maps: one per operand, the NS slice planes as outer dimension
     std::vector<CUtensorMap> maps;
     auto add_maps = [&](const __nv_bfloat16* base, long long plane, int K, long long rows, int layers, int ld,
@@ -974,7 +1019,7 @@ template <int MODE> void build_plan(Ctx& C) {
                     w.lay_rows = 0;
                     w.ldo = pad8(mRi);
                 }
-                w.out = P.x.as<__nv_bfloat16>() + p.x;
+                w.out = xbase + p.x;
                 w1.push_back(w);
             }
         const long long orr = offR[p.c][p.br];
@@ -983,13 +1028,13 @@ template <int MODE> void build_plan(Ctx& C) {
             // phase 2 operands with layers side by side: X (mLo x Tn*ldk),
             // OR (mRo x Tn*ldk); one K of Tn * ldk, padded only at its end
             const int Kc = Tn * pad8(mRi);
-            int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, Kc, mLo, 0, Kc, 0, BM);
+            int mX = add_maps(xbase + p.x, P.nx, Kc, mLo, 0, Kc, 0, BM);
             int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, Kc, mRo, 0, Kc, 0, TBN);
             s2.push_back({mX, mO, 0, 0, Kc, 1, 2, (Kc + BK - 1) / BK});
         } else {
             // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn; K
             // chunks stay inside one layer (the slices' grid is per layer row)
-            int mX = add_maps(P.x.as<__nv_bfloat16>() + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
+            int mX = add_maps(xbase + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
             int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi), TBN);
             s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
         }
@@ -1115,8 +1160,32 @@ void tc_prepare(Ctx& C, int mode) {
         GBD_CHECK_CUDA(cudaGetDevice(&dev));
         GBD_CHECK_CUDA(cudaDeviceGetAttribute(&T.n_sm, cudaDevAttrMultiProcessorCount, dev));
         T.n_sm = std::max(T.n_sm, 1);
-        T.pl[0].built = T.pl[1].built = false;
+        T.pl[0] = TcPlan();
+        T.pl[1] = TcPlan();
+        // the mixed form with sliced anchors needs the FP64 enlarged arenas only
+        // to build the operator planes (and the diagonal): when the planes and
+        // the shared phase-1 buffer would not fit beside them, both forms'
+        // planes are built side by side and each side's FP64 arena released
+        T.low_mem = false;
+        if (C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2 && !C.cfg.mixed_fp64_blocks &&
+            C.cfg.low_memory >= 0) {
+            size_t fr = 0, tot = 0;
+            GBD_CHECK_CUDA(cudaMemGetInfo(&fr, &tot));
+            const double avail = double(fr) + double(devcache_bytes());
+            const double need = H.mem_bf16x3 + H.mem_sliced + H.mem_xtc;
+            T.low_mem = C.cfg.low_memory == 1 || need > 0.85 * avail;
+        }
         H.tc_ready = true;
+    }
+    if (T.low_mem && (H.OL.resident() || H.OR.resident())) {
+        heff_diag(C);  // the diagonal reads the FP64 arenas
+        const double t0 = wall_ms();
+        for (int side = 0; side < 2; ++side) {
+            if (!T.pl[0].ops(side)) build_ops<0>(C, side);
+            if (!T.pl[1].ops(side)) build_ops<1>(C, side);
+            (side == 0 ? H.OL : H.OR).data.release();
+        }
+        C.timers[Ctx::T_PREP_SPLIT] += wall_ms() - t0;
     }
     if (!T.pl[mode].built) {
         if (mode == 0) {
@@ -1128,6 +1197,18 @@ void tc_prepare(Ctx& C, int mode) {
             C.timers[Ctx::T_TC_ISSUE_SL] = T.pl[1].issued_p1 + T.pl[1].issued_p2;
         }
     }
+}
+
+// Frees the BF16x3 operands, the shared phase-1 buffer and the split-K
+// partials of the position: after its Davidson, only the sliced operator
+// planes are still read (by the renormalisation).
+void tc_release_products(Ctx& C) {
+    TcHeff& T = C.H.tc;
+    T.pl[0] = TcPlan();
+    T.pl[1].psi.release();
+    T.pl[1].partial.release();
+    T.pl[1].built = false;
+    T.x.release();
 }
 
 namespace {
@@ -1181,7 +1262,7 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
                     double* tmp) {
     Heff& H = C.H;
     TcHeff& T = H.tc;
-    if (!H.tc_ready || !T.pl[1].built) return false;
+    if (!H.tc_ready || !T.pl[1].ops_l || !T.pl[1].ops_r) return false;
     const bool left = &O == &H.OL;
     if (!left && &O != &H.OR) return false;
     constexpr int NS = ModeCfg<1>::NS, TBN = ModeCfg<1>::BN;

@@ -83,9 +83,11 @@ struct Reduce {
 
 // Device data of one product form: slice planes, tensor maps, work lists.
 struct TcPlan {
-    bool built = false;
+    bool built = false;                         // work lists, tensor maps, psi planes
+    bool ops_l = false, ops_r = false;          // operator planes of O^Lx / O^xR
+    bool ops(int side) const { return side == 0 ? ops_l : ops_r; }
     long long nL = 0, nR = 0, np = 0, nx = 0;  // plane strides (elements) of the operator / psi / X slices
-    DevBuf ol, orr, psi, x;                     // BF16 slice planes
+    DevBuf ol, orr, psi;                        // BF16 slice planes
     DevBuf maps;                                // CUtensorMap array (64-byte aligned entries)
     DevBuf w1, s1, w2, s2, red, partial;        // work lists, segments, reductions, split-K partials
     DevBuf psi_split;                           // splitting descriptors of psi^T (one per sector)
@@ -96,6 +98,8 @@ struct TcPlan {
 
 struct TcHeff {
     TcPlan pl[2];
+    DevBuf x;                               // phase-1 output X, shared by both forms
+    bool low_mem = false;                   // FP64 enlarged arenas released after the planes were built
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
     std::vector<PsiSec> psec;
@@ -118,6 +122,7 @@ struct TcEnlSeg { const double* W; int Tin, Tout; const double* E; long long n; 
 struct TcEnlTask { double* C; long long ldc, ldr; int M, N, ncols; int seg0, nseg; };
 
 void tc_prepare(Ctx& C, int mode);
+void tc_release_products(Ctx& C);
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
 bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std::vector<long long>& toff, double* tmp);

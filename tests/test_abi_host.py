@@ -109,3 +109,42 @@ def test_export_site_returns_the_imported_blocks():
         assert kind == 1 and set(site) == set(sites[k])
         for key, blk in sites[k].items():
             assert np.array_equal(site[key], blk)
+
+
+class _FakeTensor:
+    """Stands in for a torch tensor in the binding's checks; its pointer is never used."""
+
+    def __init__(self, n, dtype, is_cuda=True):
+        self._n, self.dtype, self.is_cuda = n, dtype, is_cuda
+
+    def data_ptr(self):
+        return 0x1000
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+
+def test_pack_noalloc_binding_rejects_bad_buffers_before_the_library():
+    # the C entry point cannot see the arena's length or which memory a
+    # pointer belongs to, so the binding refuses these before any call
+    torch = pytest.importorskip("torch")
+    cls = inputs.make_env_blocks(4, 9, max_dim=20)
+    cm, bm, data = g.env_metadata(cls)
+    need = sum((cm[r[0], 2] * r[5] * r[6] + 1) // 2 * 2 for r in bm)
+    good_arena = _FakeTensor(need, torch.float64)
+    good_dst = _FakeTensor(1 << 20, torch.uint8)
+    with pytest.raises(TypeError):      # host (numpy) arena
+        g.pack_noalloc(0, 1, np.zeros(need), cm, bm, good_dst)
+    with pytest.raises(TypeError):      # CPU tensor
+        g.pack_noalloc(0, 1, torch.zeros(need, dtype=torch.float64), cm, bm, good_dst)
+    with pytest.raises(TypeError):      # wrong dtype
+        g.pack_noalloc(0, 1, _FakeTensor(need, torch.float32), cm, bm, good_dst)
+    with pytest.raises(ValueError):     # shorter than the blocks
+        g.pack_noalloc(0, 1, _FakeTensor(need - 1, torch.float64), cm, bm, good_dst)
+    with pytest.raises(TypeError):      # dst not uint8
+        g.pack_noalloc(0, 1, good_arena, cm, bm, _FakeTensor(1 << 20, torch.float64))
+    with pytest.raises(TypeError):      # dst on the host
+        g.pack_noalloc(0, 1, good_arena, cm, bm, _FakeTensor(1 << 20, torch.uint8, is_cuda=False))

@@ -92,3 +92,25 @@ def test_computed_environment_round_trip():
     assert len(s) == ctx.pack_size(0, 5)
     ctx.unpack_env(0, 5, s)
     assert ctx.env_export(0, 5).tobytes() == before.tobytes()
+
+
+def test_offload_round_trip_is_byte_exact():
+    # an environment a step saved (pack kernel into mapped pinned host memory
+    # on the IO stream), that the next step released from the device after
+    # using it, is loaded back through the offload path (unpack from pinned
+    # memory, package checksums verified) with the bytes it had before the save
+    L, N, D, b = 8, 8, 40, 2
+    h, eri = inputs.make_integrals(L, 51)
+    sites, dims = inputs.make_mps(L, N, 0, D, 52, n_left=b)
+    c = g.Context(L, N, 0, D=D, offload=True)
+    c.load_integrals(h, eri)
+    c.import_mps(sites, [0] * b + [1] * (L - b))
+    c.build_envs(b)
+    c.step(b, 1, D)                 # creates the left environment at cut b+1 and saves it
+    before = c.env_export(0, b + 1)
+    c.step(b + 1, 1, D)             # consumes it; afterwards it lives only in pinned host memory
+    h2d0 = c.io_stats()["bytes_h2d"]
+    after = c.env_export(0, b + 1)  # loaded back through the offload path
+    assert c.io_stats()["bytes_h2d"] > h2d0
+    assert after.tobytes() == before.tobytes()
+    c.close()

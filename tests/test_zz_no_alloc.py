@@ -63,6 +63,22 @@ def test_noalloc_pack_rejects_small_destination_and_oversize():
     big_bm = np.zeros((40000, 7), dtype=np.int32)
     big_bm[:, 5] = 1
     big_bm[:, 6] = 1
+    big_arena = torch.zeros(2 * 40000, dtype=torch.float64, device="cuda")
     with pytest.raises(g.GbdError) as e:
-        g.pack_noalloc(0, 1, arena, big_cm, big_bm, dst)
+        g.pack_noalloc(0, 1, big_arena, big_cm, big_bm, dst)
+    assert e.value.code == -1
+
+
+def test_noalloc_pack_rejects_misaligned_buffers():
+    # a view one double into the arena is only 8-byte aligned: refused before any launch
+    import torch
+    cls = inputs.make_env_blocks(3, 5, max_dim=10)
+    cm, bm, data = g.env_metadata(cls)
+    arena = torch.zeros(data.size + 2 * len(bm) + 2, dtype=torch.float64, device="cuda")
+    dst = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(g.GbdError) as e:
+        g.pack_noalloc(0, 1, arena[1:], cm, bm, dst)
+    assert e.value.code == -1
+    with pytest.raises(g.GbdError) as e:
+        g.pack_noalloc(0, 1, arena, cm, bm, dst[8:])
     assert e.value.code == -1
