@@ -35,6 +35,9 @@ WORKLOADS = {
     # the smallest configuration (the oracle runs it in seconds): like-for-like pair with --impl reference
     "l10_d256": dict(L=10, N=10, tsz=0, D=256, seed=1001, b=4),
     "l30_d1024": dict(L=30, N=30, tsz=0, D=1024, seed=1002, b=14),
+    # the mixed-precision configuration: 122 GB of FP64 enlarged operators at the
+    # mid-chain position, run in the low-memory mode of the mixed form
+    "l54_d2048": dict(L=54, N=54, tsz=0, D=2048, seed=1003, b=26),
     # a few-GB case of the same kernels, for profiler captures
     "small": dict(L=16, N=16, tsz=0, D=512, seed=1002, b=7),
 }
@@ -230,6 +233,69 @@ def job_value(world, flops_per_rank, ms):
     """Whole-job useful TFLOP/s: flops of all replicas over the slowest time."""
     return world * flops_per_rank / (ms * 1e-3) / 1e12
 
+def config3_probe(device, max_matvec):
+    """L=54, N=54, D=2048 at its mid-chain position (cut 26): one mixed Davidson.
+
+    Environments are renormalised on the GPU from the seeded random MPS
+    (offloaded as they are built); the Davidson starts from a random vector
+    and runs BF16x3 products with sliced anchors.  Reported: its products'
+    useful TFLOP/s, the device memory model of the position, and one product
+    of each form against FP64 on the Davidson vector (relative residual and
+    Rayleigh quotients).  Whole sweeps at this size need more device memory
+    than one GB300 holds once the truncation concentrates the kept states
+    (see the design notes), so the comparison is made at this position.
+    """
+    import torch
+
+    import inputs
+    import paper_2412_04676_gb300 as g
+    W = WORKLOADS["l54_d2048"]
+    L, N, tsz, D, b = W["L"], W["N"], W["tsz"], W["D"], W["b"]
+    t0 = time.perf_counter()
+    h, eri = inputs.make_integrals(L, W["seed"])
+    sites, dims = inputs.make_mps(L, N, tsz, D, W["seed"] + 1, n_left=b)
+    c = g.Context(L, N, tsz, D=D, precision=g.MIXED_BF16X3, offload=True, device=int(str(device).split(":")[-1]),
+                  dav_tol=1e-6, dav_max_matvec=max_matvec)
+    c.load_integrals(h, eri)
+    c.import_mps(sites, [0] * b + [1] * (L - b))
+    c.build_envs(b)
+    t_env = time.perf_counter() - t0
+    secs, info = c.tables(b)
+    tm0 = c.timers()
+    e, _, st, rc = c.davidson(b)
+    tm1 = c.timers()
+    psi, _ = c.get_psi()
+    x = torch.from_numpy(psi).to(device)
+    x = x / torch.linalg.norm(x)
+    ym = c.apply_heff(b, x, precision=g.MIXED_BF16X3)
+    ys = c.apply_heff(b, x, precision=g.SLICED_BF16)
+    y64 = c.apply_heff(b, x, precision=g.FP64)
+    tm2 = c.timers()
+    n64 = float(torch.linalg.norm(y64))
+    e64 = float(x @ y64)
+    ms_bf = tm1["products_bf16x3_ms"] - tm0["products_bf16x3_ms"]
+    n_bf = tm1["products_bf16x3_n"] - tm0["products_bf16x3_n"]
+    out = {"workload": workload_name(W) + " (the mid-chain position only)",
+           "environments_s": t_env, "psi_dim": info["dim"], "n_terms": info["n_terms"],
+           "useful_gflop_per_product": info["useful_flops"] / 1e9,
+           "device_memory_model_gb": {k: info[k] / 1e9 for k in ("mem_operators", "mem_planes_bf16x3",
+                                                                 "mem_planes_sliced", "mem_x_fp64", "mem_x_tensor")},
+           "davidson": {"energy": e, "status": rc, "matvecs": st["matvecs"], "resid": st["resid"],
+                        "ms_products": st["ms_matvec"]},
+           "bf16x3_products": int(n_bf), "bf16x3_ms_per_product": ms_bf / max(n_bf, 1),
+           "bf16x3_useful_tflops": info["useful_flops"] * n_bf / (ms_bf * 1e-3) / 1e12 if ms_bf else None,
+           "sliced_ms_per_product": (tm1["products_sliced_ms"] - tm0["products_sliced_ms"])
+                                    / max(tm1["products_sliced_n"] - tm0["products_sliced_n"], 1),
+           "fp64_ms_per_product": tm2["products_fp64_ms"] - tm1["products_fp64_ms"],
+           "vs_fp64": {"rel_resid_bf16x3": float(torch.linalg.norm(ym - y64)) / n64,
+                       "rel_resid_sliced": float(torch.linalg.norm(ys - y64)) / n64,
+                       "rayleigh_fp64": e64, "abs_dE_bf16x3": abs(float(x @ ym) - e64),
+                       "abs_dE_sliced": abs(float(x @ ys) - e64)},
+           "autotune": c.tune_info()}
+    c.close()
+    return out
+
+
 def host_link_peak(device, nbytes=1 << 30, reps=5):
     """Pinned host <-> device copy bandwidth (plain cudaMemcpyAsync through torch), best of reps."""
     import torch
@@ -364,10 +430,36 @@ def run_ours(args, rank, world, local_rank):
         pack = pk
     except Exception as e:  # measurement extra; never fatal
         pack = {"error": repr(e)}
+    # the mixed form against FP64 at the position the timed steps reached:
+    # the relative residual of one product (BF16x3 and sliced against FP64 on
+    # the current two-site vector) and the Rayleigh quotients; whole FP64
+    # sweeps at the large workloads take hours on GB300's FP64 pipe
+    fp64cmp = None
+    if args.compare_fp64 and prec == g.MIXED_BF16X3:
+        try:
+            psi_c, pb_c = ctx.get_psi()
+            xg = torch.from_numpy(psi_c).to(f"cuda:{local_rank}")
+            xg = xg / torch.linalg.norm(xg)
+            tq0 = ctx.timers()
+            ym = ctx.apply_heff(pb_c, xg, precision=g.MIXED_BF16X3)
+            ys = ctx.apply_heff(pb_c, xg, precision=g.SLICED_BF16)
+            y64 = ctx.apply_heff(pb_c, xg, precision=g.FP64)
+            tq1 = ctx.timers()
+            n64 = float(torch.linalg.norm(y64))
+            e64, em, es = float(xg @ y64), float(xg @ ym), float(xg @ ys)
+            fp64cmp = {"position": pb_c, "rel_resid_bf16x3": float(torch.linalg.norm(ym - y64)) / n64,
+                       "rel_resid_sliced": float(torch.linalg.norm(ys - y64)) / n64,
+                       "rayleigh_fp64": e64, "abs_dE_bf16x3": abs(em - e64), "abs_dE_sliced": abs(es - e64),
+                       "ms_fp64_product": tq1["products_fp64_ms"] - tq0["products_fp64_ms"],
+                       "note": "one product of each form on the current two-site vector; the mixed Davidson's "
+                               "energy comes from sliced anchor products (abs_dE_sliced)"}
+        except Exception as e:  # measurement extra; never fatal
+            fp64cmp = {"error": repr(e)}
     # end to end, on a fresh context from the same start (same warm-up, same
     # K steps, so the Davidson sees the same convergence progression): the
     # two-site vector is uploaded from pinned host memory and read back every
     # step through the public API
+    ctx_tune = ctx.tune_info()
     ctx.close()
     ctx_e = make_ctx()
     pos[0], dirs[0] = b, 1
@@ -396,6 +488,12 @@ def run_ours(args, rank, world, local_rank):
     sweep = None
     if args.sweep_config and rank == 0:
         sweep = sweep_compare(args.sweep_config)
+    cfg3 = None
+    if args.config3 and rank == 0 and args.workload != "l54_d2048":
+        try:
+            cfg3 = config3_probe(f"cuda:{local_rank}", args.max_matvec)
+        except Exception as e:  # measurement extra; never fatal
+            cfg3 = {"error": repr(e)}
     # the oracle runs only after the GPU measurements, so it never competes for host cores
     if rank == 0 and not args.no_cpu_baseline:
         ctx_mp = mp_.get_context("spawn")
@@ -512,8 +610,11 @@ def run_ours(args, rank, world, local_rank):
                      "resid_per_step": [s["resid"] for s in stats], "max_matvec": args.max_matvec,
                      "tol": args.tol},
         "host_link": link,
+        "fp64_compare": fp64cmp,
+        "autotune": ctx_tune,
         "pack": pack,
         "sweep": sweep,
+        "config3": cfg3,
         "detail": {"matvec_tflops": flops / (ms_mv * 1e-3) / 1e12 if ms_mv else 0.0, "matvecs": nmv,
                    "ms_matvec": ms_mv, "ms_device": ms_dev,
                    "wall_s": t_wall, "energy": stats[-1]["energy"],
@@ -545,6 +646,10 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-matvec", type=int, default=60)
     ap.add_argument("--fp64-peak", type=float, default=1.0975)
+    ap.add_argument("--no-config3", dest="config3", action="store_false",
+                    help="skip the L=54, D=2048 mid-chain Davidson and its FP64 comparison")
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false",
+                    help="skip the sampled mixed-vs-FP64 product comparison")
     ap.add_argument("--sweep-config", default="14,14,384,4",
                     help="L,N,D,sweeps of the FP64-vs-mixed sweep comparison ('' to skip)")
     args = ap.parse_args()

@@ -70,7 +70,10 @@ enum {
  * 2^-30 relative to the row maxima).  GBD_SLICED_BF16 is a product form for
  * gbd_apply_heff and for Davidson anchors (mixed_polish = 2), not a
  * context precision. */
-enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2 };
+enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2, GBD_FP64_PER_BLOCK = 3 };
+/* GBD_FP64_PER_BLOCK: the FP64 product with one kernel launch per sector
+ * block GEMM task instead of one grouped launch per phase (same kernel, same
+ * tiles, bitwise the same result); a comparison form for gbd_apply_heff. */
 
 typedef struct gbd_ctx gbd_ctx;
 
@@ -110,6 +113,19 @@ typedef struct {
                            and renormalisation GEMMs in the sliced form     */
     int fault_inject;   /* host-side fault injection for failure tests, 0 in
                            normal use; a sum of GBD_FAULT_* bits           */
+    int autotune;       /* 1 (default): the BF16x3 phase-2 work-list shape is
+                           chosen per position by timing candidate shapes on
+                           its first products (gbd_tune_info); the choice is
+                           cached under the position's sector-size histogram
+                           and reused; 0: the fixed default shape          */
+    int env_recompute;  /* with offload on: 0 (default) every environment is
+                           saved to the pinned host store; k >= 2: only
+                           environments at cuts divisible by k (and the two
+                           chain ends) are saved, the others are dropped
+                           after use and rebuilt when needed from the
+                           nearest saved one towards their chain end, by
+                           enlargement and renormalisation with the current
+                           site isometries (recomputation instead of IO)  */
     int low_memory;     /* mixed form with sliced anchors (mixed_polish = 2):
                            its products read only the tensor-core planes, so
                            the FP64 enlarged operators can be released once
@@ -260,8 +276,8 @@ int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n,
 /* psi_out = H_eff psi_in at position b (Sec. II.B step 2).  Vectors in the
  * sector-major layout above, FP64.  on_device = 1: both pointers are device
  * pointers; 0: host pointers (copied in and out).  precision selects the
- * product form (GBD_FP64, GBD_MIXED_BF16X3 or GBD_SLICED_BF16).  psi_out may
- * not alias psi_in. */
+ * product form (GBD_FP64, GBD_MIXED_BF16X3, GBD_SLICED_BF16 or
+ * GBD_FP64_PER_BLOCK).  psi_out may not alias psi_in. */
 int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, int on_device, int precision);
 
 /* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
@@ -381,6 +397,28 @@ int gbd_env_export(gbd_ctx* ctx, int side, int cut, double* out, size_t cap, siz
 int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const int* class_meta, int nblk,
                      const int* block_meta, void* dst, size_t cap, size_t* bytes, void* stream);
 
+/* Autotuner of the BF16x3 product at the current position.  The candidates
+ * are phase-2 work-list shapes: split_per_sm[i] split-K work items per SM and
+ * order[i] (0: items listed K range by K range across the tiles of a sector,
+ * 1: tile by tile).  While active, successive BF16x3 products use candidates
+ * 0, 1, ... and ms[i] records each one's device time; then the fastest is
+ * chosen and cached under key, a coarse hash of the sector-size histogram
+ * hist (sectors per max(rows, cols) / 64 bin, last bin open: its top bin and
+ * its second moment to within 25%) and of the operator count (to within
+ * 512), so the positions of one sweep region share a choice; a later
+ * position with the same key takes the cached choice
+ * (from_cache = 1) without trials.  default_index is the fixed shape used with
+ * autotune = 0.  Fills *out for the current position while it has tuner
+ * state, else with the last finished choice (position says which). */
+typedef struct {
+    int position, active, n_candidates, chosen, current, from_cache, default_index;
+    int split_per_sm[8], order[8];
+    double ms[8];
+    int hist[16];
+    unsigned long long key;
+} gbd_tune_info;
+int gbd_tune_info_get(gbd_ctx* ctx, gbd_tune_info* out);
+
 /* Accumulated phase timers of the context in ms, in this order: enlargement
  * planning (host), enlargement kernels, renormalisation planning (host),
  * renormalisation kernels, per-sector eigensolves, Davidson anchor products
@@ -404,7 +442,10 @@ int gbd_pack_noalloc(int side, int length, const double* arena, int ncls, const 
  * the enlargement planning (host) in three parts: coefficient links, output
  * blocks, copy and GEMM items, then the algorithmic GB the GBD_MIXED_BF16X3
  * products moved (gbd_heff_info.mixed_bytes per product: operators once,
- * psi in, H psi out), then their X overhead GB (mixed_x_bytes per product).
+ * psi in, H psi out), then their X overhead GB (mixed_x_bytes per product),
+ * then the device time (ms) and number of GBD_FP64_PER_BLOCK products,
+ * then the host wall time (ms) of environment recomputation
+ * (env_recompute) and the number of environments it rebuilt.
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

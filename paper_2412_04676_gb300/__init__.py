@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
 HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
 
-FP64, MIXED_BF16X3, SLICED_BF16 = 0, 1, 2
+FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK = 0, 1, 2, 3
 FAULT_PINNED_ALLOC, FAULT_IO_NEVER_READY, FAULT_CORRUPT_HOST_COPY = 1, 2, 4
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
@@ -36,7 +36,7 @@ class Config(C.Structure):
                 ("dav_max_matvec", C.c_int), ("offload", C.c_int), ("device", C.c_int),
                 ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong),
                 ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int), ("fault_inject", C.c_int),
-                ("low_memory", C.c_int)]
+                ("autotune", C.c_int), ("env_recompute", C.c_int), ("low_memory", C.c_int)]
 
 
 class SectorInfo(C.Structure):
@@ -57,6 +57,13 @@ class StepStats(C.Structure):
                 ("ms_truncate", C.c_double), ("ms_renorm", C.c_double), ("ms_io_exposed", C.c_double),
                 ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double),
                 ("dav_status", C.c_int)]
+
+
+class TuneInfo(C.Structure):
+    _fields_ = [("position", C.c_int), ("active", C.c_int), ("n_candidates", C.c_int), ("chosen", C.c_int),
+                ("current", C.c_int),
+                ("from_cache", C.c_int), ("default_index", C.c_int), ("split_per_sm", C.c_int * 8),
+                ("order", C.c_int * 8), ("ms", C.c_double * 8), ("hist", C.c_int * 16), ("key", C.c_ulonglong)]
 
 
 class DavStats(C.Structure):
@@ -109,6 +116,7 @@ _SIGS = {
     "gbd_io_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gbd_timers": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
+    "gbd_tune_info_get": (C.c_int, [_P, C.POINTER(TuneInfo)]),
     "gbd_pack_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, C.c_size_t,
                                    C.POINTER(C.c_size_t), _P]),
 }
@@ -229,7 +237,8 @@ class Context:
 
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
-                 mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0):
+                 mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0, autotune=True,
+                 env_recompute=0):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -239,6 +248,8 @@ class Context:
         cfg.mixed_fp64_blocks, cfg.mixed_polish = int(mixed_fp64_blocks), int(mixed_polish)
         cfg.fault_inject = int(fault_inject)
         cfg.low_memory = int(low_memory)
+        cfg.autotune = int(autotune)
+        cfg.env_recompute = int(env_recompute)
         h = C.c_void_p()
         _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
         self.h = h
@@ -404,13 +415,24 @@ class Context:
               "products_fp64_gflop", "products_bf16x3_gflop", "products_sliced_gflop", "renorm_tc_gflop",
               "enlarge_tc_gflop", "step_resident", "step_enlarge", "step_davidson", "step_rho_eig", "step_renorm",
               "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
-              "products_bf16x3_gbytes", "products_bf16x3_x_gbytes"]
+              "products_bf16x3_gbytes", "products_bf16x3_x_gbytes", "products_fp64_per_block_ms",
+              "products_fp64_per_block_n", "recompute_ms", "recompute_n"]
 
     def timers(self):
         out = np.zeros(64)
         n = C.c_int()
         _check(lib().gbd_timers(self.h, _ptr(out), 64, C.byref(n)))
         return dict(zip(self.TIMERS, out[:n.value]))
+
+    def tune_info(self):
+        """Autotuner state of the BF16x3 product at the current position (see gbd_tune_info)."""
+        t = TuneInfo()
+        _check(lib().gbd_tune_info_get(self.h, C.byref(t)))
+        n = t.n_candidates
+        return dict(position=t.position, active=bool(t.active), chosen=t.chosen, current=t.current,
+                    from_cache=bool(t.from_cache),
+                    default_index=t.default_index, key=t.key, hist=list(t.hist),
+                    candidates=[dict(split_per_sm=t.split_per_sm[i], order=t.order[i], ms=t.ms[i]) for i in range(n)])
 
     def io_stats(self):
         v = [C.c_double() for _ in range(5)]

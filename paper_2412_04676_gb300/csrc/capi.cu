@@ -65,6 +65,8 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->mixed_polish = 2;
     cfg->fault_inject = 0;
     cfg->low_memory = 0;
+    cfg->autotune = 1;
+    cfg->env_recompute = 0;
     return GBD_OK;
 }
 
@@ -82,6 +84,8 @@ int gbd_create(const gbd_config* cfg, gbd_ctx** out) {
                     GBD_ERR_ARG, "bad solver settings");
         GBD_REQUIRE(cfg->mixed_polish >= 0 && cfg->mixed_polish <= 2, GBD_ERR_ARG, "mixed_polish must be 0, 1 or 2");
         GBD_REQUIRE(cfg->low_memory >= -1 && cfg->low_memory <= 1, GBD_ERR_ARG, "low_memory must be -1, 0 or 1");
+        GBD_REQUIRE(cfg->autotune == 0 || cfg->autotune == 1, GBD_ERR_ARG, "autotune must be 0 or 1");
+        GBD_REQUIRE(cfg->env_recompute == 0 || cfg->env_recompute >= 2, GBD_ERR_ARG, "env_recompute must be 0 or >= 2");
         auto* c = new gbd_ctx();
         c->C.cfg = *cfg;
         *out = c;
@@ -210,7 +214,8 @@ int gbd_apply_heff(gbd_ctx* c, int b, const double* psi_in, double* psi_out, int
     return guard([&] {
         Ctx& C = ctx(c);
         GBD_REQUIRE(psi_in && psi_out && psi_in != psi_out, GBD_ERR_ARG, "bad vectors");
-        GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16, GBD_ERR_ARG,
+        GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 ||
+                        precision == GBD_FP64_PER_BLOCK, GBD_ERR_ARG,
                     "bad precision");
         ensure_heff(C, b);
         Heff& H = C.H;
@@ -423,6 +428,15 @@ int gbd_env_export(gbd_ctx* c, int side, int cut, double* out, size_t cap, size_
         if (elems) *elems = size_t(E->total);
         GBD_REQUIRE(out && cap >= size_t(E->total), GBD_ERR_ARG, "output too small");
         GBD_CHECK_CUDA(cudaMemcpy(out, E->data.p, size_t(E->total) * sizeof(double), cudaMemcpyDeviceToHost));
+        return GBD_OK;
+    });
+}
+
+int gbd_tune_info_get(gbd_ctx* c, gbd_tune_info* out) {
+    return guard([&] {
+        Ctx& C = ctx(c);
+        GBD_REQUIRE(out, GBD_ERR_ARG, "null output");
+        tc_tune_info(C, out);
         return GBD_OK;
     });
 }

@@ -35,6 +35,9 @@ struct Error : std::runtime_error {
         }                                                                                   \
     } while (0)
 
+// Device allocation failure with the size asked for and the device's free memory.
+[[noreturn]] void throw_device_oom(size_t bytes, const char* what);
+
 #define GBD_REQUIRE(cond, code, msg)                                   \
     do {                                                               \
         if (!(cond)) throw ::gbd::Error((code), std::string(msg));     \
@@ -174,7 +177,16 @@ struct DevBuf {
         if (n <= bytes && p) return;
         release();
         if (n == 0) n = 16;
-        GBD_CHECK_CUDA(cudaMalloc(&p, n));
+        if (cudaMalloc(&p, n) != cudaSuccess) {  // blocks held by the cache go back first
+            cudaGetLastError();
+            p = nullptr;
+            devcache_trim();
+            if (cudaMalloc(&p, n) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                throw_device_oom(n, "cudaMalloc");
+            }
+        }
         bytes = n;
     }
     // grow-only from the block cache; the block is used on stream st
@@ -190,7 +202,16 @@ struct DevBuf {
     void alloc_async(size_t n, cudaStream_t st) {
         release();
         if (n == 0) n = 16;
-        GBD_CHECK_CUDA(cudaMallocAsync(&p, n, st));
+        if (cudaMallocAsync(&p, n, st) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            devcache_trim();
+            if (cudaMallocAsync(&p, n, st) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                throw_device_oom(n, "cudaMallocAsync");
+            }
+        }
         bytes = n;
     }
     void release_async(cudaStream_t st) {

@@ -19,6 +19,7 @@
 #include <cusolverDn.h>
 
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <numeric>
 #include <random>
@@ -467,7 +468,9 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
             (void)bi;
             tmp_tot += (long long)out.cls[c].states.size() * U.basis.dim[U.basis.find(nb.Qo)] * nb.cols;
         }
-    C.scratch_tmp.ensure(size_t(std::max<long long>(tmp_tot, 1)) * sizeof(double));
+    // the intermediate is as large as the new environment times the enlarged
+    // dimension over the kept one: from the block cache, given back on return
+    C.scratch_tmp.ensure_cached(size_t(std::max<long long>(tmp_tot, 1)) * sizeof(double), C.cs);
     double* tmp = C.scratch_tmp.as<double>();
     // mixed form: both GEMM phases on the tensor cores in the sliced form when
     // the enlarged set's slices exist (FP64 GEMMs otherwise)
@@ -548,6 +551,7 @@ static void renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out) {
         PB.launch(C.cs);
     }
     GBD_CHECK_CUDA(cudaStreamSynchronize(C.cs));
+    C.scratch_tmp.release();
     C.timers[Ctx::T_REN_DEV] += wall_ms() - t_dev0;
 }
 
@@ -561,6 +565,8 @@ void ensure_cuda(Ctx& C) {
     GBD_CHECK_CUDA(cudaEventCreate(&C.ev1));
     if (cusolverDnCreate(&C.sol) != CUSOLVER_STATUS_SUCCESS) throw Error(GBD_ERR_CUDA, "cusolverDnCreate failed");
     cusolverDnSetStream(C.sol, C.cs);
+    if (cusolverDnCreateParams(&C.eig_params) != CUSOLVER_STATUS_SUCCESS)
+        throw Error(GBD_ERR_CUDA, "cusolverDnCreateParams failed");
     for (int i = 0; i < Ctx::kEigStreams; ++i) {
         GBD_CHECK_CUDA(cudaStreamCreateWithFlags(&C.eig_st[i], cudaStreamNonBlocking));
         if (cusolverDnCreate(&C.eig_sol[i]) != CUSOLVER_STATUS_SUCCESS) throw Error(GBD_ERR_CUDA, "cusolverDnCreate failed");
@@ -589,6 +595,8 @@ void destroy_ctx(Ctx& C) {
     C.hostL.clear();
     C.hostR.clear();
     if (C.sol) cusolverDnDestroy(C.sol);
+    if (C.eig_params) cusolverDnDestroyParams(C.eig_params);
+    C.eig_params = nullptr;
     for (int i = 0; i < Ctx::kEigStreams; ++i) {
         if (C.eig_sol[i]) cusolverDnDestroy(C.eig_sol[i]);
         if (C.eig_st[i]) cudaStreamDestroy(C.eig_st[i]);
@@ -838,6 +846,53 @@ void build_envs(Ctx& C, int b) {
     C.psi_valid = false;
 }
 
+// Recomputation of an environment that was dropped without a host copy
+// (env_recompute): from the nearest environment towards its chain end that
+// is resident or stored, one enlargement + renormalisation per site with the
+// current isometries (the steps of build_envs).  The environments passed on
+// the way stay resident: the sweep needs them next.
+void rebuild_env(Ctx& C, int side, int cut) {
+    const double t0 = wall_ms();
+    auto avail = [&](int c) {
+        OpSet* E = env_of(C, side, c, false);
+        if (!E) return false;
+        const HostEnv& h = side == 0 ? C.hostL[c] : C.hostR[c];
+        return E->resident() || h.valid;
+    };
+    int from = cut;
+    if (side == 0) {
+        while (from > 0 && !avail(from)) --from;
+    } else {
+        while (from < C.L && !avail(from)) ++from;
+    }
+    GBD_REQUIRE(avail(from), GBD_ERR_STATE, "no stored environment to recompute from");
+    make_resident(C, side, from);
+    int n = 0;
+    if (side == 0) {
+        for (int k = from; k < cut; ++k, ++n) {
+            GBD_REQUIRE(C.sites[k].kind == 0, GBD_ERR_STATE, "recomputation needs left-isometric sites left of the cut");
+            OpSet O;
+            EBasis eb;
+            enlarge(C, *C.envL[k], 0, k, O, eb);
+            auto E = std::make_unique<OpSet>();
+            renormalize(C, O, C.sites[k], *E);
+            C.envL[k + 1] = std::move(E);
+        }
+    } else {
+        for (int k = from - 1; k >= cut; --k, ++n) {
+            GBD_REQUIRE(C.sites[k].kind == 1, GBD_ERR_STATE, "recomputation needs right-isometric sites right of the cut");
+            OpSet O;
+            EBasis eb;
+            enlarge(C, *C.envR[k + 1], 1, k, O, eb);
+            auto E = std::make_unique<OpSet>();
+            renormalize(C, O, C.sites[k], *E);
+            C.envR[k] = std::move(E);
+        }
+    }
+    C.timers[Ctx::T_RECOMP_MS] += wall_ms() - t0;
+    C.timers[Ctx::T_RECOMP_N] += n;
+}
+
 // ============================================================== H_eff
 void setup_heff(Ctx& C, int b) {
     GBD_REQUIRE(b >= 0 && b + 1 < C.L, GBD_ERR_ARG, "two-site position out of range");
@@ -995,7 +1050,8 @@ void build_fp64_plans(Ctx& C) {
 void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     // an FP64 product after the mixed form released the FP64 enlarged
     // operators (low-memory mode) enlarges them again
-    if (precision == GBD_FP64 && !(C.H.OL.resident() && C.H.OR.resident())) setup_heff(C, C.H.b);
+    const bool fp64 = precision == GBD_FP64 || precision == GBD_FP64_PER_BLOCK;
+    if (fp64 && !(C.H.OL.resident() && C.H.OR.resident())) setup_heff(C, C.H.b);
     Heff& H = C.H;
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
@@ -1014,8 +1070,13 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
             build_fp64_plans(C);
             GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
         }
-        H.p1.launch(C.cs);
-        H.p2.launch(C.cs);
+        if (precision == GBD_FP64_PER_BLOCK) {
+            H.p1.launch_per_task(C.cs);
+            H.p2.launch_per_task(C.cs);
+        } else {
+            H.p1.launch(C.cs);
+            H.p2.launch(C.cs);
+        }
     }
     GBD_CHECK_CUDA(cudaEventRecord(C.ev1, C.cs));
     GBD_CHECK_CUDA(cudaMemcpyAsync(out, H.yout.p, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
@@ -1028,12 +1089,18 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     cudaEventElapsedTime(&ms, C.ev0, C.ev1);
     C.ms_matvec_acc += ms;
     C.matvec_count += 1;
-    C.timers[Ctx::T_PROD_MS0 + precision] += ms;
-    C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
-    C.timers[Ctx::T_PROD_GF0 + precision] += H.flops * 1e-9;
+    if (precision == GBD_FP64_PER_BLOCK) {
+        C.timers[Ctx::T_PROD_MS_PB] += ms;
+        C.timers[Ctx::T_PROD_N_PB] += 1.0;
+    } else {
+        C.timers[Ctx::T_PROD_MS0 + precision] += ms;
+        C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
+        C.timers[Ctx::T_PROD_GF0 + precision] += H.flops * 1e-9;
+    }
     if (precision == GBD_MIXED_BF16X3) {
         C.timers[Ctx::T_PROD_GB1] += H.mixed_bytes * 1e-9;
         C.timers[Ctx::T_PROD_XGB1] += H.mixed_x_bytes * 1e-9;
+        tc_tune_step(C, ms);
     }
 }
 
@@ -1354,12 +1421,13 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
 
 // ============================================================== truncation
 namespace {
-__global__ void gather_eigvec_kernel(const double* __restrict__ A, int m, int k, double* __restrict__ U) {
-    // U[i][a] = eigenvector (m-1-a) (ascending order from the eigensolver, column-major A)
+__global__ void gather_eigvec_kernel(const double* __restrict__ A, int lda, int m, int k, double* __restrict__ U) {
+    // U[i][a] = row i < m of eigenvector (lda-1-a) (ascending order from the
+    // eigensolver, column-major A of an lda x lda slot)
     long long n = (long long)m * k;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         int i = int(e / k), a = int(e % k);
-        U[e] = A[(long long)(m - 1 - a) * m + i];
+        U[e] = A[(long long)(lda - 1 - a) * lda + i];
     }
 }
 
@@ -1384,28 +1452,57 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     cudaStream_t s = C.cs;
     const double* psi = C.psi.as<double>();
     const int ns = int(H.sq.size());
-    // density matrices
-    std::vector<int> m(ns);
-    std::vector<long long> roff(ns);
-    long long rtot = 0;
+    // density matrices, grouped in size classes: sector i's m_i x m_i block
+    // sits in the top-left corner of an npad x npad slot of its class (npad =
+    // m rounded up to 16, then to 32), the rest of the slot is -I, which
+    // leaves rho's eigenpairs untouched (block diagonal) and sorts its own
+    // eigenvalues (-1) below rho's (>= 0)
+    std::vector<int> m(ns), npad(ns), cls_of(ns), slot(ns);
+    std::vector<long long> roff(ns), eoff(ns);
+    std::map<int, std::vector<int>> by_pad;  // npad -> sectors
     for (int i = 0; i < ns; ++i) {
         m[i] = dir == 1 ? H.bL.dim[H.sL[i]] : H.bR.dim[H.sR[i]];
-        roff[i] = rtot;
-        rtot += (long long)m[i] * m[i];
+        npad[i] = m[i] <= 16 ? 16 : (m[i] + 31) / 32 * 32;
+        if (m[i] > 0) by_pad[npad[i]].push_back(i);
+    }
+    struct EigClass { int n, batch; long long a0, w0; int i0; };  // i0: first info entry
+    std::vector<EigClass> ecls;
+    long long rtot = 0, etot = 0;
+    int ninfo = 0;
+    for (auto& kv : by_pad) {
+        EigClass ec{kv.first, int(kv.second.size()), rtot, etot, ninfo};
+        ninfo += ec.batch;
+        for (size_t j = 0; j < kv.second.size(); ++j) {
+            const int i = kv.second[j];
+            cls_of[i] = int(ecls.size());
+            slot[i] = int(j);
+            roff[i] = rtot + (long long)j * ec.n * ec.n;
+            eoff[i] = etot + (long long)j * ec.n;
+        }
+        rtot += (long long)ec.batch * ec.n * ec.n;
+        etot += (long long)ec.batch * ec.n;
+        ecls.push_back(ec);
     }
     DevBuf rho, evals, info;
     rho.ensure_cached(size_t(std::max<long long>(rtot, 1)) * sizeof(double), s);
-    long long etot = 0;
-    for (int i = 0; i < ns; ++i) etot += m[i];
     evals.ensure_cached(size_t(std::max<long long>(etot, 1)) * sizeof(double), s);
-    info.ensure_cached(sizeof(int) * (ns + 1), s);
+    info.ensure_cached(sizeof(int) * (ninfo + 1), s);
+    if (!C.marks.empty()) step_mark(C, Ctx::T_PH_RHO_EIG);
+    if (rtot > 0) {
+        GBD_CHECK_CUDA(cudaMemsetAsync(rho.p, 0, size_t(rtot) * sizeof(double), s));
+        std::vector<PadSeg> pads;
+        for (int i = 0; i < ns; ++i)
+            if (m[i] > 0 && npad[i] > m[i]) pads.push_back({rho.as<double>() + roff[i], npad[i], m[i]});
+        pad_identity(pads, -1.0, s);
+    }
     GemmPlan& P = C.plan_c;
     P.clear();
     for (int i = 0; i < ns; ++i) {
+        if (m[i] == 0) continue;
         int mL = H.bL.dim[H.sL[i]], mR = H.bR.dim[H.sR[i]];
         GemmTask t{};
         t.C = rho.as<double>() + roff[i];
-        t.ldc = m[i];
+        t.ldc = npad[i];
         t.M = m[i];
         t.N = m[i];
         t.nbatch = 1;
@@ -1418,46 +1515,46 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         else { g.lda = mR; g.ldb = mR; g.transA = 1; g.K = mL; }
         P.add_task(t, {g});
     }
-    if (!C.marks.empty()) step_mark(C, Ctx::T_PH_RHO_EIG);
     P.check({{C.psi.p, C.psi.bytes}, {rho.p, rho.bytes}}, "truncate/rho");
     P.upload(s);
     P.launch(s);
-    // eigen-decomposition per sector (FP64, cuSOLVER), largest sectors first,
-    // spread over several streams so the small solves overlap
+    // eigen-decomposition (FP64, cuSOLVER): one batched solve per size class,
+    // the classes spread over several streams (largest first) so they overlap
     const double t_eig0 = wall_ms();
-    std::vector<long long> eoff(ns);
-    {
-        long long eo = 0;
-        for (int i = 0; i < ns; ++i) { eoff[i] = eo; eo += m[i]; }
-    }
-    std::vector<int> order(ns);
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return m[a] > m[b]; });
     cudaEvent_t e_rho;
     GBD_CHECK_CUDA(cudaEventCreateWithFlags(&e_rho, cudaEventDisableTiming));
     GBD_CHECK_CUDA(cudaEventRecord(e_rho, s));
-    int lw_need[Ctx::kEigStreams] = {0};
-    for (int j = 0; j < ns; ++j) {
-        const int i = order[j], k = j % Ctx::kEigStreams;
-        if (m[i] == 0) continue;
-        int lw = 0;
-        if (cusolverDnDsyevd_bufferSize(C.eig_sol[k], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i],
-                                        rho.as<double>() + roff[i], m[i], evals.as<double>() + eoff[i],
-                                        &lw) != CUSOLVER_STATUS_SUCCESS)
-            throw Error(GBD_ERR_CUDA, "syevd buffer size query failed");
-        lw_need[k] = std::max(lw_need[k], lw);
+    std::vector<int> corder(ecls.size());
+    std::iota(corder.begin(), corder.end(), 0);
+    std::sort(corder.begin(), corder.end(), [&](int a, int b) { return ecls[a].n > ecls[b].n; });
+    size_t wd_need[Ctx::kEigStreams] = {0}, wh_need[Ctx::kEigStreams] = {0};
+    std::vector<size_t> wd_of(ecls.size()), wh_of(ecls.size());
+    for (size_t j = 0; j < corder.size(); ++j) {
+        const EigClass& ec = ecls[corder[j]];
+        const int k = int(j % Ctx::kEigStreams);
+        size_t wd = 0, wh = 0;
+        if (cusolverDnXsyevBatched_bufferSize(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                              ec.n, CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F,
+                                              evals.as<double>() + ec.w0, CUDA_R_64F, &wd, &wh,
+                                              ec.batch) != CUSOLVER_STATUS_SUCCESS)
+            throw Error(GBD_ERR_CUDA, "batched syev buffer size query failed");
+        wd_need[k] = std::max(wd_need[k], wd);
+        wh_need[k] = std::max(wh_need[k], wh);
     }
     for (int k = 0; k < Ctx::kEigStreams; ++k) {
-        if (size_t(lw_need[k]) * sizeof(double) > C.eig_work[k].bytes) C.eig_work[k].ensure(size_t(std::max(lw_need[k], 1)) * sizeof(double));
+        if (wd_need[k] > C.eig_work[k].bytes) C.eig_work[k].ensure(std::max<size_t>(wd_need[k], 16));
+        if (wh_need[k] > C.eig_host[k].size()) C.eig_host[k].resize(wh_need[k]);
         GBD_CHECK_CUDA(cudaStreamWaitEvent(C.eig_st[k], e_rho, 0));
     }
-    for (int j = 0; j < ns; ++j) {
-        const int i = order[j], k = j % Ctx::kEigStreams;
-        if (m[i] == 0) continue;
-        if (cusolverDnDsyevd(C.eig_sol[k], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m[i],
-                             rho.as<double>() + roff[i], m[i], evals.as<double>() + eoff[i], C.eig_work[k].as<double>(),
-                             lw_need[k], info.as<int>() + i) != CUSOLVER_STATUS_SUCCESS)
-            throw Error(GBD_ERR_CUDA, "syevd failed");
+    for (size_t j = 0; j < corder.size(); ++j) {
+        const EigClass& ec = ecls[corder[j]];
+        const int k = int(j % Ctx::kEigStreams);
+        if (cusolverDnXsyevBatched(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ec.n,
+                                   CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F, evals.as<double>() + ec.w0,
+                                   CUDA_R_64F, C.eig_work[k].p, C.eig_work[k].bytes,
+                                   C.eig_host[k].empty() ? nullptr : C.eig_host[k].data(), C.eig_host[k].size(),
+                                   info.as<int>() + ec.i0, ec.batch) != CUSOLVER_STATUS_SUCCESS)
+            throw Error(GBD_ERR_CUDA, "batched syev failed");
     }
     for (int k = 0; k < Ctx::kEigStreams; ++k) {
         cudaEvent_t e;
@@ -1468,11 +1565,15 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     }
     cudaEventDestroy(e_rho);
     std::vector<double> ev(size_t(std::max<long long>(etot, 1)));
-    std::vector<int> hinfo(ns + 1);
-    GBD_CHECK_CUDA(cudaMemcpyAsync(ev.data(), evals.p, size_t(etot) * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GBD_CHECK_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, ns * sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> hinfo(ninfo + 1);
+    if (etot > 0)
+        GBD_CHECK_CUDA(cudaMemcpyAsync(ev.data(), evals.p, size_t(etot) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (ninfo > 0)
+        GBD_CHECK_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, ninfo * sizeof(int), cudaMemcpyDeviceToHost, s));
     GBD_CHECK_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < ns; ++i) GBD_REQUIRE(hinfo[i] == 0, GBD_ERR_CUDA, "eigensolver did not converge");
+    for (int c = 0; c < ninfo; ++c) GBD_REQUIRE(hinfo[c] == 0, GBD_ERR_CUDA, "eigensolver did not converge");
+    // rho's eigenvalues are the last m_i of its slot's npad_i (ascending)
+    for (int i = 0; i < ns; ++i) eoff[i] += npad[i] - m[i];
     C.timers[Ctx::T_EIG] += wall_ms() - t_eig0;
     // global selection: descending, at most Dmax, degenerate group at the cut
     // moves the cut down, sqrt(lambda) <= 1e-13 sqrt(lambda_max) dropped
@@ -1535,7 +1636,7 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         int k = nb.dim[i];
         long long nel = (long long)m[si] * k;
         gather_eigvec_kernel<<<unsigned(std::min<long long>((nel + 255) / 256, 4096)), 256, 0, s>>>(
-            rho.as<double>() + roff[si], m[si], k, I.data.as<double>() + I.off[i]);
+            rho.as<double>() + roff[si], npad[si], m[si], k, I.data.as<double>() + I.off[i]);
         count_launch();
         int mL = H.bL.dim[H.sL[si]], mR = H.bR.dim[H.sR[si]];
         GemmTask t{};

@@ -95,6 +95,8 @@ struct Ctx {
     cudaStream_t eig_st[kEigStreams] = {nullptr};
     cusolverDnHandle_t eig_sol[kEigStreams] = {nullptr};
     DevBuf eig_work[kEigStreams];
+    std::vector<char> eig_host[kEigStreams];   // host workspace of the batched eigensolver
+    cusolverDnParams_t eig_params = nullptr;
     Heff H;
     DevBuf psi;
     bool psi_valid = false;
@@ -113,6 +115,8 @@ struct Ctx {
     double ms_matvec_acc = 0;
     int matvec_count = 0;
     bool last_dav_quick = false;  // previous mixed Davidson met its tolerance at the first anchor
+    TcTune last_tune;             // the autotuner's last finished choice (trials or cache hit)
+    int last_tune_b = -1;         // its position
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // phase timers (ms): host planning and device execution
     enum { T_ENL_HOST, T_ENL_DEV, T_REN_HOST, T_REN_DEV, T_EIG, T_POLISH, T_TCPREP, T_DAV_HOST, T_ENL_GFLOP, T_REN_GFLOP, T_TC_ISSUE1, T_TC_ISSUE2,
@@ -121,7 +125,7 @@ struct Ctx {
            T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
            // device time of the phases of gbd_step on the compute stream (host gaps included)
            T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
-           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_COUNT };
+           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_PROD_MS_PB, T_PROD_N_PB, T_RECOMP_MS, T_RECOMP_N, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};
@@ -147,6 +151,8 @@ int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* st);  // GBD_OK or G
 void collect_saves(Ctx& C, bool wait);
 void make_resident(Ctx& C, int side, int cut);  // loads an offloaded environment back (checksums verified)
 void offload_env(Ctx& C, int side, int cut);    // asynchronous save to pinned host memory, then device release
+bool env_checkpoint(const Ctx& C, int side, int cut);  // saved to the host store (env_recompute)
+void rebuild_env(Ctx& C, int side, int cut);   // recomputation from the nearest stored environment
 
 // pack / unpack (serialisation)
 size_t pack_size(const OpSet& E);

@@ -17,6 +17,7 @@
 #include "kernels.h"
 
 #include <atomic>
+#include <cstdio>
 #include <iterator>
 #include <map>
 #include <mutex>
@@ -139,6 +140,7 @@ void GemmPlan::add_task(GemmTask t, const std::vector<GemmSeg>& s) {
     if (t.nseg == 0 && t.beta != 0.0) return;  // nothing to add, C unchanged
     int id = int(tasks.size());
     tasks.push_back(t);
+    task_tile0.push_back(int(tiles.size()));
     for (int b = 0; b < t.nbatch; ++b)
         for (int m0 = 0; m0 < t.M; m0 += BM)
             for (int n0 = 0; n0 < t.N; n0 += BN) tiles.push_back({id, b, m0, n0});
@@ -194,6 +196,18 @@ void GemmPlan::launch(cudaStream_t st) const {
     gemm_f64_kernel<<<unsigned(n), NT, 0, st>>>((const GemmTask*)d_tasks, (const GemmSeg*)d_segs,
                                                 (const GemmTile*)d_tiles);
     count_launch();
+    GBD_CHECK_CUDA(cudaGetLastError());
+}
+
+void GemmPlan::launch_per_task(cudaStream_t st) const {
+    for (size_t k = 0; k < task_tile0.size(); ++k) {
+        const int t0 = task_tile0[k];
+        const int t1 = k + 1 < task_tile0.size() ? task_tile0[k + 1] : int(tiles.size());
+        if (t1 <= t0) continue;
+        gemm_f64_kernel<<<unsigned(t1 - t0), NT, 0, st>>>((const GemmTask*)d_tasks, (const GemmSeg*)d_segs,
+                                                          (const GemmTile*)d_tiles + t0);
+        count_launch();
+    }
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -504,6 +518,27 @@ void unpack_launch(const unsigned char* base, const PackItem* d_items, const Pac
     GBD_CHECK_CUDA(cudaGetLastError());
 }
 
+// ============================================================== padded slots
+namespace {
+__global__ void pad_identity_kernel(const PadSeg* __restrict__ segs, int n, double value) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const PadSeg sg = segs[i];
+        for (int d = sg.m + threadIdx.x; d < sg.n; d += blockDim.x) sg.p[(long long)d * sg.n + d] = value;
+    }
+}
+}  // namespace
+
+void pad_identity(const std::vector<PadSeg>& segs, double value, cudaStream_t st) {
+    if (segs.empty()) return;
+    PadSeg* d = nullptr;
+    GBD_CHECK_CUDA(cudaMallocAsync(&d, segs.size() * sizeof(PadSeg), st));
+    GBD_CHECK_CUDA(cudaMemcpyAsync(d, segs.data(), segs.size() * sizeof(PadSeg), cudaMemcpyHostToDevice, st));
+    pad_identity_kernel<<<unsigned(std::min<size_t>(segs.size(), 4096)), 128, 0, st>>>(d, int(segs.size()), value);
+    count_launch();
+    GBD_CHECK_CUDA(cudaGetLastError());
+    GBD_CHECK_CUDA(cudaFreeAsync(d, st));
+}
+
 // ============================================================== device block cache
 namespace {
 struct CacheBlock {
@@ -540,10 +575,22 @@ void* devcache_get(size_t n, cudaStream_t st, size_t* got) {
     if (cudaMalloc(&p, n) != cudaSuccess) {
         cudaGetLastError();
         devcache_trim();
-        GBD_CHECK_CUDA(cudaMalloc(&p, n));
+        if (cudaMalloc(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            throw_device_oom(n, "cudaMalloc (block cache)");
+        }
     }
     *got = n;
     return p;
+}
+
+void throw_device_oom(size_t bytes, const char* what) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) cudaGetLastError();
+    char buf[200];
+    snprintf(buf, sizeof(buf), "%s of %.2f GB failed: device has %.2f GB free of %.2f GB", what, bytes * 1e-9,
+             fr * 1e-9, tot * 1e-9);
+    throw Error(GBD_ERR_DEVICE_OOM, buf);
 }
 
 void devcache_put(void* p, size_t bytes, cudaStream_t st) {

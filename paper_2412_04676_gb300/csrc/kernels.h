@@ -48,10 +48,13 @@ struct GemmPlan {
     size_t cap_tasks = 0, cap_segs = 0, cap_tiles = 0;
     cudaStream_t st_last = nullptr;  // stream of the last upload (the tables' users)
     double flops = 0.0;  // 2*M*N*K summed (useful)
-    void clear() { tasks.clear(); segs.clear(); tiles.clear(); flops = 0.0; }
+    void clear() { tasks.clear(); segs.clear(); tiles.clear(); task_tile0.clear(); flops = 0.0; }
     void add_task(GemmTask t, const std::vector<GemmSeg>& s);
     void upload(cudaStream_t st);
     void launch(cudaStream_t st) const;
+    // the same tiles, one launch per task (comparison against batching)
+    void launch_per_task(cudaStream_t st) const;
+    std::vector<int> task_tile0;  // first tile of each task
     // Host-side check, before any launch, that every address a task reads or
     // writes lies inside one of the given buffers (base, bytes).
     void check(const std::vector<std::pair<const void*, size_t>>& bufs, const char* what) const;
@@ -71,6 +74,7 @@ struct GemmPlan {
         tasks = std::move(o.tasks);
         segs = std::move(o.segs);
         tiles = std::move(o.tiles);
+        task_tile0 = std::move(o.task_tile0);
         d_tasks = o.d_tasks; d_segs = o.d_segs; d_tiles = o.d_tiles;
         cap_tasks = o.cap_tasks; cap_segs = o.cap_segs; cap_tiles = o.cap_tiles;
         st_last = o.st_last;
@@ -160,6 +164,15 @@ struct CopyItem {
 constexpr int kCopyLayers = 8;
 void copy_sum(const CopyItem* d_items, int n_items, int max_tout, const CopyLink* d_links, const CopyCol* d_cols,
               const CopyCoef* d_coefs, cudaStream_t st);
+
+// ------------------------------------------------------------------ padded slots
+// Writes value on the diagonal entries m..n-1 of the column-major n x n slot
+// at p (the rest of the slot is set by the caller).
+struct PadSeg {
+    double* p;
+    int n, m;
+};
+void pad_identity(const std::vector<PadSeg>& segs, double value, cudaStream_t st);
 
 // ------------------------------------------------------------------ misc
 // Count of this library's kernel launches (incremented by every launcher).

@@ -356,6 +356,38 @@ void release_async(Ctx& C, int side, int cut) {
     E->data.release_async(C.ios);
 }
 
+// Releases the device arena of an environment that has no host copy; it is
+// rebuilt when needed (env_recompute).
+void drop_async(Ctx& C, int side, int cut) {
+    OpSet* E = env_of(C, side, cut, false);
+    if (!E || !E->resident()) return;
+    cudaEvent_t used;
+    GBD_CHECK_CUDA(cudaEventCreateWithFlags(&used, cudaEventDisableTiming));
+    GBD_CHECK_CUDA(cudaEventRecord(used, C.cs));
+    GBD_CHECK_CUDA(cudaStreamWaitEvent(C.ios, used, 0));
+    cudaEventDestroy(used);
+    E->data.release_async(C.ios);
+}
+
+// A new environment goes to the host store, or (env_recompute, not a
+// checkpoint) any older host copy of its id is invalidated.
+void store_env(Ctx& C, int side, int cut) {
+    if (env_checkpoint(C, side, cut)) {
+        save_async(C, side, cut);
+    } else {
+        HostEnv& h = host_of(C, side, cut);
+        wait_event(C, h.done);
+        h.valid = false;
+    }
+}
+
+// Releases an environment after its last use: kept in the host store, or
+// (env_recompute) dropped to be rebuilt.
+void retire_env(Ctx& C, int side, int cut) {
+    if (C.cfg.env_recompute && !env_checkpoint(C, side, cut)) drop_async(C, side, cut);
+    else release_async(C, side, cut);
+}
+
 // Load on demand (Sec. III.B.4): walk the self-contained headers on the host,
 // then unpack from mapped pinned memory on the IO stream; the checksums are
 // verified when the environment is first used.
@@ -413,6 +445,10 @@ void ensure_resident(Ctx& C, int side, int cut) {
     OpSet* E = env_of(C, side, cut, false);
     GBD_REQUIRE(E, GBD_ERR_STATE, "environment never built");
     HostEnv& h = host_of(C, side, cut);
+    if (!E->resident() && !h.valid && C.cfg.env_recompute) {
+        rebuild_env(C, side, cut);  // recomputation instead of IO
+        return;
+    }
     if (!E->resident()) load_async(C, side, cut);
     if (h.pending) {
         wait_event(C, h.loaded);
@@ -425,10 +461,17 @@ void ensure_resident(Ctx& C, int side, int cut) {
 }  // namespace
 
 // Saves an environment to the pinned host store and releases its device
-// arena once the save and every use already enqueued have finished.
+// arena once the save and every use already enqueued have finished (with
+// env_recompute, only checkpoints are saved; the others are dropped).
 void offload_env(Ctx& C, int side, int cut) {
-    save_async(C, side, cut);
-    release_async(C, side, cut);
+    store_env(C, side, cut);
+    retire_env(C, side, cut);
+}
+
+bool env_checkpoint(const Ctx& C, int side, int cut) {
+    (void)side;
+    const int k = C.cfg.env_recompute;
+    return k < 2 || cut == 0 || cut == C.L || cut % k == 0;
 }
 
 // An environment made resident for the caller: if it lives only in the
@@ -480,8 +523,8 @@ int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
     step_mark(C, Ctx::T_PH_ENLARGE);
     if (C.H.b != b || !C.H.OL.resident()) setup_heff(C, b);
     if (off) {  // both environments are consumed by the enlargement
-        release_async(C, 0, b);
-        release_async(C, 1, b + 2);
+        retire_env(C, 0, b);
+        retire_env(C, 1, b + 2);
     }
     double t1 = now_ms();
     double e = 0.0;
@@ -500,10 +543,10 @@ int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
             int need_side = dir == 1 ? 1 : 0;
             int need_cut = dir == 1 ? nb + 2 : nb;
             OpSet* nE = env_of(C, need_side, need_cut, false);
-            if (nE && !nE->resident()) load_async(C, need_side, need_cut);
+            if (nE && !nE->resident() && host_of(C, need_side, need_cut).valid) load_async(C, need_side, need_cut);
         }
-        if (dir == 1) save_async(C, 0, b + 1);
-        else save_async(C, 1, b + 1);
+        if (dir == 1) store_env(C, 0, b + 1);
+        else store_env(C, 1, b + 1);
     }
     step_mark(C, Ctx::T_PH_IO);  // closing mark
     GBD_CHECK_CUDA(cudaEventRecord(eb, C.cs));
@@ -544,7 +587,7 @@ int sweep(Ctx& C, int nsweeps, int D, gbd_sweep_stats* stats) {
     build_envs(C, 0);  // right environments for cuts L..2, left at cut 0
     const bool off = C.cfg.offload != 0;
     if (off)
-        for (int c = 2; c <= L; ++c) save_async(C, 1, c);
+        for (int c = 2; c <= L; ++c) store_env(C, 1, c);
     // start vector on (0, 1) from B_0 B_1 (host, from the imported blocks)
     setup_heff(C, 0);
     {

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 
@@ -870,6 +871,76 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
     T.blk_b.upload(st);
 }
 
+// tensor-core GFLOP a work list issues (whole 128-row tiles at the MMA width,
+// every split or slice product): the gap to the useful flops is padding
+template <int MODE> double issued_gflop(const std::vector<Work>& ws) {
+    constexpr int TBN = ModeCfg<MODE>::BN;
+    double f = 0.0;
+    for (const auto& w : ws) {
+        const int v = w.N - w.n0;
+        const int nn = v >= TBN ? TBN : ((v + 15) & ~15);  // the kernel's MMA width
+        f += double(w.c1 - w.c0) * BM * nn * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
+    }
+    return f * 1e-9;
+}
+
+// ---- autotuner of the BF16x3 phase-2 work list over the sector sizes.
+// Candidates: split-K items per SM (chunks per item = total / (k * SMs)) and
+// the listing order of the items (K range by K range across the tiles of a
+// sector, so tiles reading the same chunks run together, or tile by tile).
+struct TuneCand { int split_per_sm, order; };
+constexpr TuneCand kTuneCands[] = {{2, 0}, {4, 0}, {8, 0}, {2, 1}, {4, 1}, {8, 1}};
+constexpr int kTuneN = int(sizeof(kTuneCands) / sizeof(kTuneCands[0]));
+constexpr int kTuneDefault = 1;  // the fixed shape: 4 items per SM, K-range order
+static_assert(kTuneN <= 8, "gbd_tune_info holds 8 candidates");
+
+std::mutex g_tune_mu;
+std::map<unsigned long long, int> g_tune_cache;  // sector-size histogram key -> chosen candidate
+
+TuneParams tune_params(const TcTune& t) {
+    const int i = t.cur >= 0 ? t.cur : kTuneDefault;
+    return TuneParams{kTuneCands[i].split_per_sm, kTuneCands[i].order};
+}
+
+// Histogram of the position's sector sizes (max(rows, cols) in bins of 64,
+// the last bin open) and the operator count bucket: the tuning key.
+void tune_begin(Ctx& C) {
+    Heff& H = C.H;
+    TcTune& t = H.tc.tune;
+    t = TcTune();
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        const int m = std::max(H.bL.dim[H.sL[q]], H.bR.dim[H.sR[q]]);
+        t.hist[std::min(m / 64, 15)] += 1;
+    }
+    // the key is coarse on purpose: positions of one sweep region, whose
+    // bond dimensions change a little at every truncation, share it.  It
+    // takes the largest sector (in 64-row bins), the total of the histogram
+    // weighted by bin (a size moment, within 25%) and the layer count (within
+    // 512).
+    unsigned long long k = 1469598103934665603ULL;  // FNV-1a
+    auto mix = [&](unsigned long long v) { k = (k ^ v) * 1099511628211ULL; };
+    int top = 0;
+    double moment = 0.0;
+    for (int i = 0; i < 16; ++i)
+        if (t.hist[i]) { top = i; moment += double(t.hist[i]) * (i + 1) * (i + 1); }
+    mix((unsigned long long)top);
+    mix((unsigned long long)std::lround(std::log(std::max(moment, 1.0)) / std::log(1.25)));
+    mix((unsigned long long)C.mpo.bond_dim(H.b + 1) / 512);
+    t.key = k;
+    if (!C.cfg.autotune) { t.cur = -1; return; }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(k);
+    if (it != g_tune_cache.end()) {
+        t.cur = t.chosen = it->second;
+        t.from_cache = true;
+        C.last_tune = t;
+        C.last_tune_b = H.b;
+    } else {
+        t.active = true;
+        t.cur = 0;
+    }
+}
+
 // Operator slice planes of one product form for one side (0: O^Lx, 1:
 // O^xR), split from the FP64 enlarged arena of that side.
 template <int MODE> void build_ops(Ctx& C, int side) {
@@ -915,6 +986,95 @@ template <int MODE> void build_ops(Ctx& C, int side) {
     }
     P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
     (side == 0 ? P.ops_l : P.ops_r) = true;
+}
+
+// Phase-2 work list of one product form: per output sector tile, the K
+// chunks of all its (class, input sector) segments split into near-equal
+// ranges (split-K), one FP64 reduction per tile.
+template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
+    constexpr int TBN = ModeCfg<MODE>::BN;
+    Heff& H = C.H;
+    TcHeff& T = H.tc;
+    TcPlan& P = T.pl[MODE];
+    cudaStream_t st = C.cs;
+    const std::vector<KSeg>& s2 = P.s2_host;
+    const std::vector<std::vector<int>>& seg_of_out = P.seg_of_out;
+    std::vector<Work> w2;
+    std::vector<Reduce> red;
+    long long total_chunks = 0;
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        long long c = 0;
+        for (int si : seg_of_out[q]) c += s2[si].nchunk;
+        int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + TBN - 1) / TBN);
+        total_chunks += c * tiles;
+    }
+    const long long target = std::max<long long>(16, total_chunks / ((long long)tp.split_per_sm * T.n_sm) + 1);
+    std::vector<KSeg> s2o;  // segments re-laid per output sector (contiguous)
+    long long npart = 0;
+    for (size_t q = 0; q < H.sq.size(); ++q) {
+        int seg0 = int(s2o.size());
+        int nchunk = 0;
+        for (int si : seg_of_out[q]) { s2o.push_back(s2[si]); nchunk += s2[si].nchunk; }
+        int nseg = int(s2o.size()) - seg0;
+        const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
+        // one reduction (and a run of partials) per output tile; order 0 lists
+        // the items K range by K range, so the tiles of one sector that read
+        // the same K chunks of X and O^xR run side by side and share them in
+        // L2; order 1 lists them tile by tile
+        const int nrange = int((nchunk + target - 1) / target);
+        const size_t r0 = red.size();
+        for (int m0 = 0; m0 < mL; m0 += BM)
+            for (int n0 = 0; n0 < mR; n0 += TBN) {
+                Reduce r{};
+                r.out = H.yout.as<double>() + H.soff[q];
+                r.ldo = mR;
+                r.m0 = m0;
+                r.n0 = n0;
+                r.M = mL;
+                r.N = mR;
+                r.bn = TBN;
+                r.p0 = int(npart);
+                npart += nrange;
+                r.p1 = int(npart);
+                red.push_back(r);
+            }
+        const size_t r1 = red.size();
+        auto item = [&](size_t ti, int k) {
+            const Reduce& r = red[ti];
+            const int c0 = int(k * target);
+            Work w{};
+            w.m0 = r.m0;
+            w.n0 = r.n0;
+            w.M = mL;
+            w.N = mR;
+            w.seg0 = seg0;
+            w.nseg = nseg;
+            w.c0 = c0;
+            w.c1 = int(std::min<long long>(nchunk, c0 + target));
+            w.out_kind = 0;
+            w.promote = MODE == 0 ? 8 : 1;
+            w.ldo = TBN;
+            w.colcap = TBN;
+            w.out = reinterpret_cast<void*>((long long)r.p0 + k);  // patched to a pointer below
+            w2.push_back(w);
+        };
+        if (tp.order == 0) {
+            for (int k = 0; k < nrange; ++k)
+                for (size_t ti = r0; ti < r1; ++ti) item(ti, k);
+        } else {
+            for (size_t ti = r0; ti < r1; ++ti)
+                for (int k = 0; k < nrange; ++k) item(ti, k);
+        }
+    }
+    P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
+    for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
+    P.issued_p2 = issued_gflop<MODE>(w2);
+    upload_vec(P.w2, w2, st);
+    upload_vec(P.s2, s2o, st);
+    upload_vec(P.red, red, st);
+    P.n_w2 = int(w2.size());
+    P.n_red = int(red.size());
+    GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the host vectors are freed on return
 }
 
 // Slice planes, tensor maps and work lists of one product form.
@@ -983,8 +1143,7 @@ template <int MODE> void build_plan(Ctx& C) {
         psi_map[s] = add_maps(P.psi.as<__nv_bfloat16>() + ps.dst, P.np, ps.mL, ps.mR, 0, ps.ldp, 0, TBN);
     }
     std::vector<KSeg> s1, s2;
-    std::vector<Work> w1, w2;
-    std::vector<Reduce> red;
+    std::vector<Work> w1;
     std::vector<std::vector<int>> seg_of_out(H.sq.size());
     for (const auto& p : pairs) {
         const OpClass& cl = H.OL.cls[p.c];
@@ -1039,79 +1198,13 @@ template <int MODE> void build_plan(Ctx& C) {
             s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
         }
     }
-    // phase 2 work: per output sector tile, K split into near-equal chunk ranges
-    long long total_chunks = 0;
-    for (size_t q = 0; q < H.sq.size(); ++q) {
-        long long c = 0;
-        for (int si : seg_of_out[q]) c += s2[si].nchunk;
-        int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + TBN - 1) / TBN);
-        total_chunks += c * tiles;
-    }
-    const long long target = std::max<long long>(16, total_chunks / (4 * T.n_sm) + 1);
-    std::vector<KSeg> s2o;  // segments re-laid per output sector (contiguous)
-    long long npart = 0;
-    for (size_t q = 0; q < H.sq.size(); ++q) {
-        int seg0 = int(s2o.size());
-        int nchunk = 0;
-        for (int si : seg_of_out[q]) { s2o.push_back(s2[si]); nchunk += s2[si].nchunk; }
-        int nseg = int(s2o.size()) - seg0;
-        const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
-        // one reduction (and a run of partials) per output tile; the items are
-        // listed K range by K range, so the tiles of one sector that read the
-        // same K chunks of X and O^xR run side by side and share them in L2
-        const int nrange = int((nchunk + target - 1) / target);
-        const size_t r0 = red.size();
-        for (int m0 = 0; m0 < mL; m0 += BM)
-            for (int n0 = 0; n0 < mR; n0 += TBN) {
-                Reduce r{};
-                r.out = H.yout.as<double>() + H.soff[q];
-                r.ldo = mR;
-                r.m0 = m0;
-                r.n0 = n0;
-                r.M = mL;
-                r.N = mR;
-                r.bn = TBN;
-                r.p0 = int(npart);
-                npart += nrange;
-                r.p1 = int(npart);
-                red.push_back(r);
-            }
-        for (int k = 0; k < nrange; ++k)
-            for (size_t ti = r0; ti < red.size(); ++ti) {
-                const Reduce& r = red[ti];
-                const int c0 = int(k * target);
-                Work w{};
-                w.m0 = r.m0;
-                w.n0 = r.n0;
-                w.M = mL;
-                w.N = mR;
-                w.seg0 = seg0;
-                w.nseg = nseg;
-                w.c0 = c0;
-                w.c1 = int(std::min<long long>(nchunk, c0 + target));
-                w.out_kind = 0;
-                w.promote = MODE == 0 ? 8 : 1;
-                w.ldo = TBN;
-                w.colcap = TBN;
-                w.out = reinterpret_cast<void*>((long long)r.p0 + k);  // patched to a pointer below
-                w2.push_back(w);
-            }
-    }
-    P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
-    for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
+    P.s2_host = s2;
+    P.seg_of_out = seg_of_out;
     // tensor-core work issued per product (whole 128-row tiles at the MMA
     // width, every slice product): the gap to the useful flops is padding
-    auto issued = [](const std::vector<Work>& ws) {
-        double f = 0.0;
-        for (const auto& w : ws) {
-            const int v = w.N - w.n0;
-            const int nn = v >= TBN ? TBN : ((v + 15) & ~15);  // the kernel's MMA width
-            f += double(w.c1 - w.c0) * BM * nn * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
-        }
-        return f * 1e-9;
-    };
-    P.issued_p1 = issued(w1);
-    P.issued_p2 = issued(w2);
+    P.issued_p1 = issued_gflop<MODE>(w1);
+    if (MODE == 0) tune_begin(C);
+    build_p2<MODE>(C, MODE == 0 ? tune_params(H.tc.tune) : TuneParams{});
     // persistent CTAs take items round-robin: w1 is longest first by
     // construction (pairs sorted by K), w2 keeps its K-range grouping
     const double t2 = wall_ms();
@@ -1119,12 +1212,7 @@ template <int MODE> void build_plan(Ctx& C) {
     upload_vec(P.maps, maps, st);
     upload_vec(P.w1, w1, st);
     upload_vec(P.s1, s1, st);
-    upload_vec(P.w2, w2, st);
-    upload_vec(P.s2, s2o, st);
-    upload_vec(P.red, red, st);
     P.n_w1 = int(w1.size());
-    P.n_w2 = int(w2.size());
-    P.n_red = int(red.size());
     GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         KT<MODE, 1>::SMEM_BYTES));
     GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1197,6 +1285,53 @@ void tc_prepare(Ctx& C, int mode) {
             C.timers[Ctx::T_TC_ISSUE_SL] = T.pl[1].issued_p1 + T.pl[1].issued_p2;
         }
     }
+}
+
+// After each BF16x3 product: while the tuner is trying candidates, record
+// this product's device time and move to the next candidate; after the last
+// one, keep the fastest (cached under the sector-size histogram key).
+void tc_tune_step(Ctx& C, double ms) {
+    TcTune& t = C.H.tc.tune;
+    if (!t.active) return;
+    t.ms[t.cur] = ms;
+    int next = t.cur + 1;
+    if (next < kTuneN) {
+        t.cur = next;
+    } else {
+        int best = 0;
+        for (int i = 1; i < kTuneN; ++i)
+            if (t.ms[i] < t.ms[best]) best = i;
+        t.chosen = best;
+        t.cur = best;
+        t.active = false;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[t.key] = best;
+        C.last_tune = t;
+        C.last_tune_b = C.H.b;
+    }
+    build_p2<0>(C, tune_params(t));
+    C.timers[Ctx::T_TC_ISSUE2] = C.H.tc.pl[0].issued_p2;
+}
+
+void tc_tune_info(Ctx& C, gbd_tune_info* out) {
+    // the current position's state while it has one, else the last finished choice
+    const bool cur = C.H.tc_ready && C.H.tc.tune.key != 0;
+    const TcTune& t = cur ? C.H.tc.tune : C.last_tune;
+    std::memset(out, 0, sizeof(*out));
+    out->position = cur ? C.H.b : C.last_tune_b;
+    out->active = t.active ? 1 : 0;
+    out->n_candidates = kTuneN;
+    out->chosen = t.chosen;
+    out->current = t.cur;
+    out->from_cache = t.from_cache ? 1 : 0;
+    out->default_index = kTuneDefault;
+    out->key = t.key;
+    for (int i = 0; i < kTuneN; ++i) {
+        out->split_per_sm[i] = kTuneCands[i].split_per_sm;
+        out->order[i] = kTuneCands[i].order;
+        out->ms[i] = t.ms[i];
+    }
+    for (int i = 0; i < 16; ++i) out->hist[i] = t.hist[i];
 }
 
 // Frees the BF16x3 operands, the shared phase-1 buffer and the split-K
@@ -1433,6 +1568,8 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
     }
     GBD_CHECK_CUDA(cudaGetLastError());
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the tables above are freed on return
+    T.ren_u.release();
+    T.ren_t.release();
     const int e = tc_error(C);
     GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core renormalisation stopped on a bounded wait (code " + std::to_string(e) + ")");
     return true;
@@ -1462,8 +1599,8 @@ void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::ve
     }
     nw = std::max(nw, 8LL);
     ne = std::max(ne, 8LL);
-    C.env_sl_w.ensure(size_t(nw) * NS * 2);
-    C.env_sl_e.ensure(size_t(ne) * NS * 2);
+    C.env_sl_w.ensure_cached(size_t(nw) * NS * 2, st);
+    C.env_sl_e.ensure_cached(size_t(ne) * NS * 2, st);
     C.env_err.ensure(sizeof(int));
     GBD_CHECK_CUDA(cudaMemsetAsync(C.env_err.p, 0, sizeof(int), st));
     // slicing: W^T row c = column c of W; E^T row e = column e of E
@@ -1544,6 +1681,8 @@ void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::ve
     count_launch();
     GBD_CHECK_CUDA(cudaGetLastError());
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the tables above are freed on return
+    C.env_sl_w.release();  // sliced operands go back to the block cache
+    C.env_sl_e.release();
     int e = 0;
     GBD_CHECK_CUDA(cudaMemcpy(&e, C.env_err.p, sizeof(int), cudaMemcpyDeviceToHost));
     GBD_REQUIRE(e == 0, GBD_ERR_CUDA, "tensor-core enlargement stopped on a bounded wait (code " + std::to_string(e) + ")");

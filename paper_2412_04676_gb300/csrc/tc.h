@@ -81,6 +81,23 @@ struct Reduce {
 
 }  // namespace tc
 
+// Phase-2 work-list shape (autotuned for the BF16x3 form).
+struct TuneParams {
+    int split_per_sm = 4;  // split-K work items per SM
+    int order = 0;         // 0: items K range by K range across a sector's tiles, 1: tile by tile
+};
+
+// Autotuner state of the position: candidate times, choice, histogram key.
+struct TcTune {
+    bool active = false;     // still trying candidates
+    bool from_cache = false; // choice taken from an earlier position with the same key
+    int cur = -1;            // candidate the current work list uses (-1: fixed default)
+    int chosen = -1;
+    double ms[8] = {0};
+    int hist[16] = {0};      // sectors per max(rows, cols) / 64 bin
+    unsigned long long key = 0;
+};
+
 // Device data of one product form: slice planes, tensor maps, work lists.
 struct TcPlan {
     bool built = false;                         // work lists, tensor maps, psi planes
@@ -94,11 +111,14 @@ struct TcPlan {
     int n_w1 = 0, n_w2 = 0, n_red = 0, n_psi = 0;
     double bytes_ops = 0.0;                     // operator slice bytes
     double issued_p1 = 0.0, issued_p2 = 0.0;    // tensor-core GFLOP issued per product
+    std::vector<tc::KSeg> s2_host;              // phase-2 segments per pair (host, for re-planning)
+    std::vector<std::vector<int>> seg_of_out;   // phase-2 segments of each output sector
 };
 
 struct TcHeff {
     TcPlan pl[2];
     DevBuf x;                               // phase-1 output X, shared by both forms
+    TcTune tune;                            // BF16x3 phase-2 autotuner
     bool low_mem = false;                   // FP64 enlarged arenas released after the planes were built
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
@@ -123,6 +143,8 @@ struct TcEnlTask { double* C; long long ldc, ldr; int M, N, ncols; int seg0, nse
 
 void tc_prepare(Ctx& C, int mode);
 void tc_release_products(Ctx& C);
+void tc_tune_step(Ctx& C, double ms);       // after each BF16x3 product
+void tc_tune_info(Ctx& C, gbd_tune_info* out);
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
 bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std::vector<long long>& toff, double* tmp);

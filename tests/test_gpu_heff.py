@@ -69,3 +69,22 @@ def test_heff_hermitian_full_size_l30_d1024():
     H2 = ctx.apply_heff(b, 2.0 * x - 3.0 * z)
     assert np.abs(H2 - (2 * Hx - 3 * Hz)).max() <= 1e-11 * np.abs(H2).max()
     assert info["n_terms"] > 1000 and info["useful_flops"] > 1e10
+
+
+def test_per_block_launches_give_the_batched_result():
+    # the comparison form: every sector block GEMM task in its own launch
+    # (same kernel, same tiles) is bitwise the grouped product
+    import paper_2412_04676_gb300 as g
+    L, N, tsz, D, b = 10, 10, 0, 120, 4
+    c = heff_case(L, N, tsz, D, 108, b)
+    ctx, He = c["ctx"], c["He"]
+    x = He.flatten(He.to_enlarged(c["psi4"], None))
+    y = ctx.apply_heff(b, x, precision=g.FP64)
+    n0 = g.launch_count()
+    yb = ctx.apply_heff(b, x, precision=g.FP64_PER_BLOCK)
+    n1 = g.launch_count()
+    assert np.array_equal(y, yb)
+    secs, info = ctx.tables(b)
+    assert n1 - n0 > len(secs)          # at least one launch per output sector
+    t = ctx.timers()
+    assert t["products_fp64_per_block_n"] == 1 and t["products_fp64_per_block_ms"] > 0
