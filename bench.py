@@ -47,7 +47,11 @@ METRIC = "H_eff psi useful TFLOP/s over whole two-site DMRG steps (mixed BF16x3 
 # DRAM traffic of one BF16x3 H_eff product (phase-1 + phase-2 kernels) from
 # one ncu capture of a small case, scaled to the workload by its operator
 # bytes; valid only while the kernel source is the one that was measured.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/tc_gemm_bf16x3_l30_d1024.md: mean of eight products at cut 14
+    "l30_d1024": {"tc_cu": "6cabe0bc2f7e47a8", "bytes_per_product": 21.49e9,
+                  "source": "profiles/tc_gemm_bf16x3_l30_d1024.md (ncu, full-size workload, one-pass metrics)"},
+}
 
 
 def workload_name(W):
@@ -486,12 +490,12 @@ def run_ours(args, rank, world, local_rank):
         psi = out
     ctx_e.close()
     sweep = None
-    if args.sweep_config and rank == 0:
+    if args.sweep_config.strip("'\" ") and rank == 0:
         sweep = sweep_compare(args.sweep_config)
     cfg3 = None
     if args.config3 and rank == 0 and args.workload != "l54_d2048":
         try:
-            cfg3 = config3_probe(f"cuda:{local_rank}", args.max_matvec)
+            cfg3 = config3_probe(f"cuda:{local_rank}", args.config3_max_matvec)
         except Exception as e:  # measurement extra; never fatal
             cfg3 = {"error": repr(e)}
     # the oracle runs only after the GPU measurements, so it never competes for host cores
@@ -534,7 +538,8 @@ def run_ours(args, rank, world, local_rank):
             traffic = tr["bytes_per_product"]
         roofs["bf16x3"] = {
             "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-            "traffic": traffic, "ms": f["ms"], "launches": n,
+            "traffic": traffic, "traffic_source": tr["source"] if traffic else "no capture of this kernel build",
+            "ms": f["ms"], "launches": n,
             "kernel": "tc_gemm_kernel<0, 1> + <0, 2> (+ split, reduce): BF16x3 H_eff product",
             "peak_source": f"{peak_src}: bf16 sustained / 3 (three split products per useful flop; "
                            "the product is timed inside whole steps)",
@@ -648,6 +653,8 @@ def main():
     ap.add_argument("--fp64-peak", type=float, default=1.0975)
     ap.add_argument("--no-config3", dest="config3", action="store_false",
                     help="skip the L=54, D=2048 mid-chain Davidson and its FP64 comparison")
+    ap.add_argument("--config3-max-matvec", type=int, default=200,
+                    help="product limit of the L=54, D=2048 Davidson (it starts from a random vector)")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false",
                     help="skip the sampled mixed-vs-FP64 product comparison")
     ap.add_argument("--sweep-config", default="14,14,384,4",

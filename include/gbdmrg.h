@@ -126,6 +126,13 @@ typedef struct {
                            nearest saved one towards their chain end, by
                            enlargement and renormalisation with the current
                            site isometries (recomputation instead of IO)  */
+    long long host_store_bytes; /* with offload on: 0 (default) no bound on the
+                           pinned host memory of saved environments; > 0: at
+                           most this many bytes stay pinned, the least
+                           recently used saved environments go to a spill
+                           file (one per context, in $TMPDIR or /tmp,
+                           removed with the process) through an IO thread
+                           and are read back when a step needs them        */
     int low_memory;     /* mixed form with sliced anchors (mixed_polish = 2):
                            its products read only the tensor-core planes, so
                            the FP64 enlarged operators can be released once
@@ -445,7 +452,9 @@ int gbd_tune_info_get(gbd_ctx* ctx, gbd_tune_info* out);
  * psi in, H psi out), then their X overhead GB (mixed_x_bytes per product),
  * then the device time (ms) and number of GBD_FP64_PER_BLOCK products,
  * then the host wall time (ms) of environment recomputation
- * (env_recompute) and the number of environments it rebuilt.
+ * (env_recompute) and the number of environments it rebuilt, then the GB
+ * written to and read back from the spill file and the host time (ms) spent
+ * waiting for spill jobs (host_store_bytes).
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("dav_max_matvec", C.c_int), ("offload", C.c_int), ("device", C.c_int),
                 ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong),
                 ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int), ("fault_inject", C.c_int),
-                ("autotune", C.c_int), ("env_recompute", C.c_int), ("low_memory", C.c_int)]
+                ("autotune", C.c_int), ("env_recompute", C.c_int), ("host_store_bytes", C.c_longlong),
+                ("low_memory", C.c_int)]
 
 
 class SectorInfo(C.Structure):
@@ -238,7 +239,7 @@ class Context:
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
                  mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0, autotune=True,
-                 env_recompute=0):
+                 env_recompute=0, host_store_bytes=0):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -250,6 +251,7 @@ class Context:
         cfg.low_memory = int(low_memory)
         cfg.autotune = int(autotune)
         cfg.env_recompute = int(env_recompute)
+        cfg.host_store_bytes = int(host_store_bytes)
         h = C.c_void_p()
         _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
         self.h = h
@@ -416,7 +418,8 @@ class Context:
               "enlarge_tc_gflop", "step_resident", "step_enlarge", "step_davidson", "step_rho_eig", "step_renorm",
               "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
               "products_bf16x3_gbytes", "products_bf16x3_x_gbytes", "products_fp64_per_block_ms",
-              "products_fp64_per_block_n", "recompute_ms", "recompute_n"]
+              "products_fp64_per_block_n", "recompute_ms", "recompute_n", "spill_gbytes", "restore_gbytes",
+              "spill_wait_ms"]
 
     def timers(self):
         out = np.zeros(64)

@@ -67,6 +67,7 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->low_memory = 0;
     cfg->autotune = 1;
     cfg->env_recompute = 0;
+    cfg->host_store_bytes = 0;
     return GBD_OK;
 }
 
@@ -86,6 +87,7 @@ int gbd_create(const gbd_config* cfg, gbd_ctx** out) {
         GBD_REQUIRE(cfg->low_memory >= -1 && cfg->low_memory <= 1, GBD_ERR_ARG, "low_memory must be -1, 0 or 1");
         GBD_REQUIRE(cfg->autotune == 0 || cfg->autotune == 1, GBD_ERR_ARG, "autotune must be 0 or 1");
         GBD_REQUIRE(cfg->env_recompute == 0 || cfg->env_recompute >= 2, GBD_ERR_ARG, "env_recompute must be 0 or >= 2");
+        GBD_REQUIRE(cfg->host_store_bytes >= 0, GBD_ERR_ARG, "host_store_bytes must be >= 0");
         auto* c = new gbd_ctx();
         c->C.cfg = *cfg;
         *out = c;

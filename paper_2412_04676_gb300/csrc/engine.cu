@@ -588,8 +588,10 @@ void destroy_ctx(Ctx& C) {
         if (h.loaded) cudaEventDestroy(h.loaded);
         h = HostEnv();
     };
+    C.spill.reset();  // its IO thread finishes queued jobs before the buffers go
     for (auto& h : C.hostL) free_host(h);
     for (auto& h : C.hostR) free_host(h);
+    C.pinned_bytes = 0;
     for (auto& ps : C.saves) { cudaEventDestroy(ps.a); cudaEventDestroy(ps.b); }
     C.saves.clear();
     C.hostL.clear();

@@ -10,6 +10,7 @@
 #include "core.h"
 #include "kernels.h"
 #include "mpo.h"
+#include "spill.h"
 #include "tc.h"
 
 namespace gbd {
@@ -43,6 +44,13 @@ struct HostEnv {
     bool pending = false;            // load enqueued, not yet verified
     cudaEvent_t loaded = nullptr;
     std::vector<unsigned long long> want;
+    // bounded store (host_store_bytes): the packed stream may live in the spill file
+    bool spilled = false;            // payload only in the spill file (host == nullptr)
+    bool restoring = false;          // read back into `host` in flight (job)
+    std::shared_ptr<SpillJob> job;   // spill write or restore read in flight
+    long long file_off = -1;         // this id's region of the spill file
+    size_t file_cap = 0;
+    unsigned long long stamp = 0;    // last save or load, for the choice of spill victims
 };
 
 // Enlarged operators and product plans at one two-site position b.
@@ -89,6 +97,9 @@ struct Ctx {
     std::vector<int> site_kind;
     std::vector<std::unique_ptr<OpSet>> envL, envR;
     std::vector<HostEnv> hostL, hostR;
+    std::unique_ptr<SpillStore> spill;   // created at the first spill
+    size_t pinned_bytes = 0;             // packed-stream buffers of the host store
+    unsigned long long io_stamp = 0;
     cudaStream_t cs = nullptr, ios = nullptr;
     cusolverDnHandle_t sol = nullptr;
     static constexpr int kEigStreams = 16;
@@ -125,7 +136,8 @@ struct Ctx {
            T_REN_TC_GFLOP, T_ENL_TC_GFLOP,
            // device time of the phases of gbd_step on the compute stream (host gaps included)
            T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
-           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_PROD_MS_PB, T_PROD_N_PB, T_RECOMP_MS, T_RECOMP_N, T_COUNT };
+           T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_PROD_MS_PB, T_PROD_N_PB, T_RECOMP_MS, T_RECOMP_N,
+           T_SPILL_GB, T_RESTORE_GB, T_SPILL_WAIT_MS, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};

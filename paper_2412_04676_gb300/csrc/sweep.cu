@@ -276,6 +276,93 @@ void pinned_grow(const Ctx& C, unsigned char*& p, size_t& cap, size_t need) {
     cap = c;
 }
 
+// ---- bounded host store (host_store_bytes) and its spill file
+
+SpillStore& spill_of(Ctx& C) {
+    if (!C.spill) C.spill = std::make_unique<SpillStore>();
+    return *C.spill;
+}
+
+// Waits for h's spill job (bounded by io_timeout_ms, counted as exposed IO);
+// a finished write frees the pinned copy, a finished read makes it valid.
+void finish_job(Ctx& C, HostEnv& h) {
+    if (!h.job) return;
+    const double t0 = now_ms();
+    const int st = SpillStore::wait(h.job, C.cfg.io_timeout_ms);
+    const double dt = now_ms() - t0;
+    C.io_exposed_ms += dt;
+    C.timers[Ctx::T_SPILL_WAIT_MS] += dt;
+    if (st == 0) throw Error(GBD_ERR_TIMEOUT, "spill file job wait timed out");
+    if (st < 0) throw Error(GBD_ERR_HOST_OOM, "spill file read or write failed");
+    if (h.job->write) {
+        cudaFreeHost(h.host);
+        C.pinned_bytes -= h.cap;
+        h.host = nullptr;
+        h.cap = 0;
+        h.spilled = true;
+        C.timers[Ctx::T_SPILL_GB] += double(h.bytes) * 1e-9;
+    } else {
+        h.spilled = false;
+        h.restoring = false;
+        C.timers[Ctx::T_RESTORE_GB] += double(h.bytes) * 1e-9;
+    }
+    h.job.reset();
+}
+
+// Frees the pinned copies whose spill writes have finished (no wait).
+void reap_spills(Ctx& C) {
+    for (auto* v : {&C.hostL, &C.hostR})
+        for (auto& h : *v)
+            if (h.job && h.job->write && h.job->state.load() != 0) finish_job(C, h);
+}
+
+// Makes room for `need` more pinned bytes: the least recently used saved
+// environments whose saves have finished are written to the spill file;
+// their pinned copies go once the writes finish.  The bound is soft: with
+// nothing left to spill the store grows past it.
+void make_room(Ctx& C, size_t need, const HostEnv* self) {
+    const long long budget = C.cfg.host_store_bytes;
+    if (budget <= 0) return;
+    reap_spills(C);
+    while ((long long)(C.pinned_bytes + need) > budget) {
+        HostEnv* victim = nullptr;
+        for (auto* v : {&C.hostL, &C.hostR})
+            for (auto& h : *v) {
+                if (&h == self || !h.host || !h.valid || h.job || h.pending || h.restoring) continue;
+                if (h.done && cudaEventQuery(h.done) != cudaSuccess) { cudaGetLastError(); continue; }  // save running
+                if (!victim || h.stamp < victim->stamp) victim = &h;
+            }
+        if (victim) {
+            size_t cap = 0;
+            victim->file_off = spill_of(C).region(victim->file_off, victim->file_cap, victim->bytes, &cap);
+            victim->file_cap = cap;
+            victim->job = spill_of(C).submit(true, victim->host, victim->bytes, victim->file_off);
+        }
+        // the oldest write in flight frees its copy
+        HostEnv* oldest = nullptr;
+        for (auto* v : {&C.hostL, &C.hostR})
+            for (auto& h : *v)
+                if (h.job && h.job->write && (!oldest || h.stamp < oldest->stamp)) oldest = &h;
+        if (!oldest) break;
+        finish_job(C, *oldest);
+    }
+}
+
+// The pinned buffer of h's packed stream, within the store's bound.
+void host_alloc(Ctx& C, HostEnv& h, size_t need) {
+    if (h.host && need <= h.cap) return;
+    if (h.host) {
+        cudaFreeHost(h.host);
+        C.pinned_bytes -= h.cap;
+        h.host = nullptr;
+        h.cap = 0;
+    }
+    const size_t c = C.cfg.host_store_bytes > 0 ? need : std::max<size_t>(need, 64);
+    make_room(C, c, &h);
+    pinned_grow(C, h.host, h.cap, c);
+    C.pinned_bytes += h.cap;
+}
+
 template <class T> T* dev_view(void* host) {
     void* d = nullptr;
     GBD_CHECK_CUDA(cudaHostGetDevicePointer(&d, host, 0));
@@ -313,9 +400,13 @@ void save_async(Ctx& C, int side, int cut) {
     HostEnv& h = host_of(C, side, cut);
     wait_event(C, h.done);
     if (h.pending) wait_event(C, h.loaded);
+    finish_job(C, h);  // a spill or restore of the old content in flight
     PackHost P;
     build_pack(C, *E, P);
-    pinned_grow(C, h.host, h.cap, std::max<size_t>(P.total, 64));
+    h.spilled = false;
+    h.restoring = false;
+    h.stamp = ++C.io_stamp;
+    host_alloc(C, h, std::max<size_t>(P.total, 64));
     if (!h.done) GBD_CHECK_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
     h.bytes = P.total;
     h.npk = int(P.items.size());
@@ -397,6 +488,18 @@ void load_async(Ctx& C, int side, int cut) {
     if (E->resident()) return;
     HostEnv& h = host_of(C, side, cut);
     GBD_REQUIRE(h.valid, GBD_ERR_STATE, "environment neither resident nor saved");
+    h.stamp = ++C.io_stamp;
+    if (h.job && h.job->write) finish_job(C, h);  // a spill of it in flight
+    if (h.spilled) {
+        // read back into pinned memory on the IO thread; the unpack follows
+        // when the step needs it (ensure_resident)
+        if (!h.restoring) {
+            host_alloc(C, h, h.bytes);
+            h.job = spill_of(C).submit(false, h.host, h.bytes, h.file_off);
+            h.restoring = true;
+        }
+        return;
+    }
     wait_event(C, h.done);  // "fetching": the save must have finished
     size_t n = size_t(std::max<long long>(E->total, 2)) * sizeof(double);
     E->data.alloc_async(n, C.ios);
@@ -449,7 +552,13 @@ void ensure_resident(Ctx& C, int side, int cut) {
         rebuild_env(C, side, cut);  // recomputation instead of IO
         return;
     }
-    if (!E->resident()) load_async(C, side, cut);
+    if (!E->resident()) {
+        load_async(C, side, cut);
+        if (h.restoring) {  // residency checkpoint: the restore must have finished
+            finish_job(C, h);
+            load_async(C, side, cut);
+        }
+    }
     if (h.pending) {
         wait_event(C, h.loaded);
         for (size_t i = 0; i < h.want.size(); ++i)

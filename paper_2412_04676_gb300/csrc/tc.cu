@@ -40,14 +40,17 @@ constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at 2 GHz
 // item per tile, no split-K).
 template <int MODE, int PH> struct KT {
     static constexpr int NS = ModeCfg<MODE>::NS;
-    static constexpr int BN = ModeCfg<MODE>::BN;
-    static constexpr int BUFCOLS = ModeCfg<MODE>::BUFCOLS;
-    static constexpr int TMEM_COLS = ModeCfg<MODE>::TMEM_COLS;
+    static constexpr int BN = PH == 2 ? ModeCfg<MODE>::BN2 : ModeCfg<MODE>::BN;
+    static constexpr int BUFCOLS = PH == 2 ? ModeCfg<MODE>::BUFCOLS2 : ModeCfg<MODE>::BUFCOLS;
+    static constexpr int TMEM_COLS = PH == 2 ? ModeCfg<MODE>::TMEM_COLS2 : ModeCfg<MODE>::TMEM_COLS;
+    // BF16x3 phase 2 sums its promotions in plain FP32 (the form's own error
+    // is 2^-16); the sliced form keeps error-free (hi, lo) pairs
+    static constexpr bool PAIRS = !(PH == 2 && MODE == 0);
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NS * (A_BYTES + B_BYTES);
     static constexpr int CP = BN / 4;                        // accumulator columns per epilogue thread
-    static constexpr int ST = (PH == 2 && MODE == 0) ? 3 : 2;  // PH 3: FP64 output straight from registers
+    static constexpr int ST = 2;  // PH 2 / 3: output straight from registers
     static constexpr int RS = BN * 2;                        // row stride of a BF16 staging plane (XOR-swizzled)
     static constexpr int NPL = PH == 1 ? (MODE == 0 ? 2 : 1) : 0;  // staging planes
     static constexpr int EPI_BYTES = NPL * BM * RS;
@@ -366,9 +369,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 ndrain = n > 0 ? (n + promote - 1) / promote : 0;
                 nn = tile_n_of<K_::BN>(works[wi].N, works[wi].n0);  // TMEM columns the MMAs wrote
             }
-            float ah[CP], al[CP];
+            float ah[CP], al[K_::PAIRS ? CP : 1];
 #pragma unroll
-            for (int i = 0; i < CP; ++i) { ah[i] = 0.f; al[i] = 0.f; }
+            for (int i = 0; i < CP; ++i) ah[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < (K_::PAIRS ? CP : 1); ++i) al[i] = 0.f;
             bool gave_up = false;
             for (int dd = 0; dd < ndrain; ++dd, ++D) {
                 const int buf = D & 1;
@@ -389,9 +394,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         tmem_ld16(tb + c * 16, r);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            // phase 1 drains once (K = one block dimension): plain FP32
-                            if constexpr (PH == 1) ah[c * 16 + i] += __uint_as_float(r[i]);
-                            else two_sum_acc(ah[c * 16 + i], al[c * 16 + i], __uint_as_float(r[i]));
+                            // phase 1 drains once (K = one block dimension), phase 2
+                            // promotes every few chunks: plain FP32 sums
+                            ah[c * 16 + i] += __uint_as_float(r[i]);
                         }
                     }
                 } else {
@@ -438,12 +443,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                     }
                 }
             } else if constexpr (PH == 2) {
-                // partial tile of (hi, lo) pairs, column-pair-major: a warp
-                // writes 512 contiguous bytes per store
-                float4* out = reinterpret_cast<float4*>(w.out);
+                if constexpr (K_::PAIRS) {
+                    // partial tile of (hi, lo) pairs, column-pair-major: a warp
+                    // writes 512 contiguous bytes per store
+                    float4* out = reinterpret_cast<float4*>(w.out);
 #pragma unroll
-                for (int i = 0; i < CP; i += 2)
-                    out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
+                    for (int i = 0; i < CP; i += 2)
+                        out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float4(ah[i], al[i], ah[i + 1], al[i + 1]);
+                } else {
+                    // partial tile of FP32 sums, column-pair-major (256 contiguous bytes per warp store)
+                    float2* out = reinterpret_cast<float2*>(w.out);
+#pragma unroll
+                    for (int i = 0; i < CP; i += 2)
+                        out[(long long)(part * (CP / 2) + i / 2) * BM + row] = make_float2(ah[i], ah[i + 1]);
+                }
             } else {
                 __nv_bfloat16* o0 = reinterpret_cast<__nv_bfloat16*>(w.out);
                 const long long ldo = w.ldo;
@@ -684,8 +697,8 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
     }
 }
 
-// partial tiles hold FP32 (hi, lo) pairs, column-pair-major: element (i, j)
-// at pair index ((j / 2) * BM + i) * 2 + (j % 2)
+// partial tiles hold FP32 (hi, lo) pairs (or FP32 sums), column-pair-major:
+// element (i, j) at index ((j / 2) * BM + i) * 2 + (j % 2)
 // grid (tiles, kReduceSplit): CTA y sums rows y, y + kReduceSplit, ... of its tile
 constexpr int kReduceSplit = 16;
 
@@ -699,9 +712,14 @@ __global__ void reduce_kernel(const Reduce* __restrict__ red, const float2* __re
             if (gj >= r.N) break;
             const long long idx = ((long long)(j / 2) * BM + i) * 2 + (j % 2);
             double v = 0.0;
-            for (int p = r.p0; p < r.p1; ++p) {
-                const float2 x = partial[(long long)p * BM * r.bn + idx];
-                v += double(x.x) + double(x.y);
+            if (r.pairs) {
+                for (int p = r.p0; p < r.p1; ++p) {
+                    const float2 x = partial[(long long)p * BM * r.bn + idx];
+                    v += double(x.x) + double(x.y);
+                }
+            } else {
+                const float* pf = reinterpret_cast<const float*>(partial);
+                for (int p = r.p0; p < r.p1; ++p) v += double(pf[(long long)p * BM * r.bn + idx]);
             }
             r.out[(long long)gi * r.ldo + gj] = v;
         }
@@ -873,8 +891,8 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
 
 // tensor-core GFLOP a work list issues (whole 128-row tiles at the MMA width,
 // every split or slice product): the gap to the useful flops is padding
-template <int MODE> double issued_gflop(const std::vector<Work>& ws) {
-    constexpr int TBN = ModeCfg<MODE>::BN;
+template <int MODE, int PH> double issued_gflop(const std::vector<Work>& ws) {
+    constexpr int TBN = PH == 2 ? ModeCfg<MODE>::BN2 : ModeCfg<MODE>::BN;
     double f = 0.0;
     for (const auto& w : ws) {
         const int v = w.N - w.n0;
@@ -992,7 +1010,8 @@ template <int MODE> void build_ops(Ctx& C, int side) {
 // chunks of all its (class, input sector) segments split into near-equal
 // ranges (split-K), one FP64 reduction per tile.
 template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
-    constexpr int TBN = ModeCfg<MODE>::BN;
+    constexpr int TBN = ModeCfg<MODE>::BN2;
+    constexpr bool pairs = KT<MODE, 2>::PAIRS;
     Heff& H = C.H;
     TcHeff& T = H.tc;
     TcPlan& P = T.pl[MODE];
@@ -1033,6 +1052,7 @@ template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
                 r.M = mL;
                 r.N = mR;
                 r.bn = TBN;
+                r.pairs = pairs ? 1 : 0;
                 r.p0 = int(npart);
                 npart += nrange;
                 r.p1 = int(npart);
@@ -1066,9 +1086,11 @@ template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
                 for (int k = 0; k < nrange; ++k) item(ti, k);
         }
     }
+    // partial tiles: float2 (hi, lo) per element, or one float per element
     P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
-    for (auto& w : w2) w.out = P.partial.as<float2>() + reinterpret_cast<long long>(w.out) * BM * TBN;
-    P.issued_p2 = issued_gflop<MODE>(w2);
+    for (auto& w : w2)
+        w.out = reinterpret_cast<float*>(P.partial.p) + reinterpret_cast<long long>(w.out) * BM * TBN * (pairs ? 2 : 1);
+    P.issued_p2 = issued_gflop<MODE, 2>(w2);
     upload_vec(P.w2, w2, st);
     upload_vec(P.s2, s2o, st);
     upload_vec(P.red, red, st);
@@ -1188,13 +1210,14 @@ template <int MODE> void build_plan(Ctx& C) {
             // OR (mRo x Tn*ldk); one K of Tn * ldk, padded only at its end
             const int Kc = Tn * pad8(mRi);
             int mX = add_maps(xbase + p.x, P.nx, Kc, mLo, 0, Kc, 0, BM);
-            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, Kc, mRo, 0, Kc, 0, TBN);
+            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, Kc, mRo, 0, Kc, 0, ModeCfg<MODE>::BN2);
             s2.push_back({mX, mO, 0, 0, Kc, 1, 2, (Kc + BK - 1) / BK});
         } else {
             // phase 2 operands: X_t (mLo x mRi), OR_t (mRo x mRi), layers Tn; K
             // chunks stay inside one layer (the slices' grid is per layer row)
             int mX = add_maps(xbase + p.x, P.nx, mRi, mLo, Tn, pad8(mRi), (long long)mLo * pad8(mRi), BM);
-            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi), TBN);
+            int mO = add_maps(P.orr.as<__nv_bfloat16>() + orr, P.nR, mRi, mRo, Tn, pad8(mRi), (long long)mRo * pad8(mRi),
+                              ModeCfg<MODE>::BN2);
             s2.push_back({mX, mO, 0, 0, mRi, Tn, 3, Tn * ((mRi + BK - 1) / BK)});
         }
     }
@@ -1202,7 +1225,7 @@ template <int MODE> void build_plan(Ctx& C) {
     P.seg_of_out = seg_of_out;
     // tensor-core work issued per product (whole 128-row tiles at the MMA
     // width, every slice product): the gap to the useful flops is padding
-    P.issued_p1 = issued_gflop<MODE>(w1);
+    P.issued_p1 = issued_gflop<MODE, 1>(w1);
     if (MODE == 0) tune_begin(C);
     build_p2<MODE>(C, MODE == 0 ? tune_params(H.tc.tune) : TuneParams{});
     // persistent CTAs take items round-robin: w1 is longest first by

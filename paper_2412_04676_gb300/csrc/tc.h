@@ -36,9 +36,17 @@ constexpr int THREADS = 64 + EPI_THREADS;    // warp 0 TMA, warp 1 MMA, then the
 
 // per-mode tile shape: slices per operand, tile columns, TMEM columns per
 // buffer, pipeline stages (as many as fit in shared memory)
+// BN2 / BUFCOLS2 / TMEM_COLS2: the phase-2 tile of the form (BF16x3: 256
+// columns, so a sector of up to 256 columns reads its X rows once).
 template <int MODE> struct ModeCfg;
-template <> struct ModeCfg<0> { static constexpr int NS = 2, BN = 128, BUFCOLS = 128, TMEM_COLS = 256, STAGES = 3; };
-template <> struct ModeCfg<1> { static constexpr int NS = 4, BN = 64, BUFCOLS = 256, TMEM_COLS = 512, STAGES = 2; };
+template <> struct ModeCfg<0> {
+    static constexpr int NS = 2, BN = 128, BUFCOLS = 128, TMEM_COLS = 256, STAGES = 3;
+    static constexpr int BN2 = 256, BUFCOLS2 = 256, TMEM_COLS2 = 512;
+};
+template <> struct ModeCfg<1> {
+    static constexpr int NS = 4, BN = 64, BUFCOLS = 256, TMEM_COLS = 512, STAGES = 2;
+    static constexpr int BN2 = 64, BUFCOLS2 = 256, TMEM_COLS2 = 512;
+};
 
 // One K segment: chunks over layers t < T and inner offsets j0 < K step BK.
 struct KSeg {
@@ -77,6 +85,7 @@ struct Reduce {
     int m0, n0, M, N;
     int p0, p1;        // partial tiles [p0, p1)
     int bn;            // tile columns
+    int pairs;         // 1: partial elements are FP32 (hi, lo) pairs; 0: FP32 sums
 };
 
 }  // namespace tc

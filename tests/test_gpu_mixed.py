@@ -1,12 +1,14 @@
-"""Mixed-precision (BF16x3 split, FP32 accumulation with FP64 promotion) H_eff
-products on the tensor cores, against the FP64 path and the oracle.
+"""Mixed-precision (BF16x3 split, FP32 accumulation, FP64 split-K reduction)
+H_eff products on the tensor cores, against the FP64 path and the oracle.
 
 Error model (stated bound): each operand is split x = hi + lo with
 |x - hi - lo| <= 2^-18 |x|; a product keeps hi*hi + hi*lo + lo*hi, dropping
-lo*lo <= 2^-18 |a b|; the phase-1 output is re-split (2^-18); FP32 sums run
-over at most 8 chunks of 64 before promotion to FP64 (<= 512 * 2^-24 per
-sum).  Elementwise |y_mixed - y| <= c * (|O^Lx| |psi| |O^xR|^T) with
-c = 1e-4 covers 3 * 2^-16 + 600 * 2^-24 with margin.
+lo*lo <= 2^-18 |a b|; the phase-1 output is re-split (2^-18); the tensor
+cores sum at most 8 chunks of 64 in FP32 before each promotion (<= 512 *
+2^-24 per sum), the promotions of one split-K item add in FP32 (a few tens,
+2^-24 each) and the items in FP64.  Elementwise
+|y_mixed - y| <= c * (|O^Lx| |psi| |O^xR|^T) with c = 1e-4 covers
+3 * 2^-16 + 600 * 2^-24 with margin.
 """
 import numpy as np
 import pytest
