@@ -134,6 +134,24 @@ def sweep_compare(spec):
         ctx.close()
     out["abs_dE"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
     out["speedup_last_sweep"] = out["fp64"]["ms_per_sweep"][-1] / out["mixed"]["ms_per_sweep"][-1]
+    # the environment-store options on the mixed form: recomputation from every
+    # second environment, and a pinned store bounded to a quarter of one
+    # sweep's saved bytes (the rest spilled to a file)
+    bound = int(out["mixed"]["bytes_packed"] / nsw / 4)
+    for name, kw in (("mixed_recompute2", dict(env_recompute=2)), ("mixed_spill", dict(host_store_bytes=bound))):
+        ctx = g.Context(L, N, 0, D=D, precision=g.MIXED_BF16X3, offload=True, dav_tol=1e-8, **kw)
+        ctx.load_integrals(h, eri)
+        ctx.import_mps(sites, [1] * L)
+        st = ctx.sweep(nsw, D)
+        t = ctx.timers()
+        out[name] = {"ms_per_sweep": [x["ms_total"] for x in st], "energy": st[-1]["energy_last"],
+                     "ms_io_exposed": sum(x["ms_io_exposed"] for x in st),
+                     "bytes_packed": sum(x["bytes_packed"] for x in st),
+                     "recomputed": t["recompute_n"], "recompute_ms": t["recompute_ms"],
+                     "spill_gb": t["spill_gbytes"], "restore_gb": t["restore_gbytes"],
+                     "spill_wait_ms": t["spill_wait_ms"], "host_store_bytes": kw.get("host_store_bytes", 0)}
+        out[name]["abs_dE_vs_mixed"] = abs(out[name]["energy"] - out["mixed"]["energy"])
+        ctx.close()
     return out
 
 
@@ -448,6 +466,7 @@ def run_ours(args, rank, world, local_rank):
             ym = ctx.apply_heff(pb_c, xg, precision=g.MIXED_BF16X3)
             ys = ctx.apply_heff(pb_c, xg, precision=g.SLICED_BF16)
             y64 = ctx.apply_heff(pb_c, xg, precision=g.FP64)
+            ypb = ctx.apply_heff(pb_c, xg, precision=g.FP64_PER_BLOCK)
             tq1 = ctx.timers()
             n64 = float(torch.linalg.norm(y64))
             e64, em, es = float(xg @ y64), float(xg @ ym), float(xg @ ys)
@@ -455,6 +474,9 @@ def run_ours(args, rank, world, local_rank):
                        "rel_resid_sliced": float(torch.linalg.norm(ys - y64)) / n64,
                        "rayleigh_fp64": e64, "abs_dE_bf16x3": abs(em - e64), "abs_dE_sliced": abs(es - e64),
                        "ms_fp64_product": tq1["products_fp64_ms"] - tq0["products_fp64_ms"],
+                       "ms_fp64_per_block_product": tq1["products_fp64_per_block_ms"]
+                                                    - tq0["products_fp64_per_block_ms"],
+                       "per_block_bitwise_equal": bool(torch.equal(ypb, y64)),
                        "note": "one product of each form on the current two-site vector; the mixed Davidson's "
                                "energy comes from sliced anchor products (abs_dE_sliced)"}
         except Exception as e:  # measurement extra; never fatal
@@ -611,6 +633,10 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "clocks": clk,
         "davidson": {"converged_steps": sum(1 for x in status if x == 0), "steps": len(status),
+                     "at_product_limit": sum(1 for x in status if x == 1),
+                     "at_precision_floor": sum(1 for x in status if x == 2),
+                     "status_note": "0: residual <= tol; 1: product limit; 2: mixed form stopped after three "
+                                    "anchors above tol (its rounding floor)",
                      "status_per_step": status, "matvecs_per_step": [s["matvecs"] for s in stats],
                      "resid_per_step": [s["resid"] for s in stats], "max_matvec": args.max_matvec,
                      "tol": args.tol},

@@ -57,7 +57,11 @@ enum {
     GBD_ERR_TIMEOUT = -5,      /* a bounded wait on an IO event ran out          */
     GBD_ERR_CORRUPT = -6,      /* package magic / checksum / metadata mismatch   */
     GBD_ERR_STATE = -7,        /* call out of order (e.g. no integrals loaded)   */
-    GBD_WARN_NOT_CONVERGED = 1 /* Davidson hit its product limit                 */
+    GBD_WARN_NOT_CONVERGED = 1, /* Davidson hit its product limit                */
+    GBD_WARN_PRECISION_FLOOR = 2 /* mixed Davidson: after three anchors the exact
+                                    residual is still above dav_tol (the floor
+                                    the BF16x3 products leave); the energy is the
+                                    last anchor's Rayleigh quotient            */
 };
 
 /* H_eff product forms.  GBD_FP64: FP64 GEMMs.  GBD_MIXED_BF16X3: every
@@ -224,7 +228,9 @@ typedef struct {
     double bytes_packed;    /* environment bytes serialised to host this step    */
     double ms_device;       /* CUDA-event span of the step on the compute stream */
     int dav_status;         /* GBD_OK: Davidson converged; GBD_WARN_NOT_CONVERGED:
-                               it stopped at its product limit              */
+                               it stopped at its product limit;
+                               GBD_WARN_PRECISION_FLOOR: the mixed form's
+                               anchors stopped above dav_tol                */
 } gbd_step_stats;
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -294,7 +300,9 @@ int gbd_heff_diagonal(gbd_ctx* ctx, int b, double* diag, int on_device);
 /* Lowest eigenpair of H_eff at b.  psi (host, sector-major) is the start
  * vector on entry (NULL = library's current two-site vector or random) and
  * the normalised eigenvector on exit (may be NULL).  Returns
- * GBD_WARN_NOT_CONVERGED if the product limit was reached. */
+ * GBD_WARN_NOT_CONVERGED if the product limit was reached, and in the mixed
+ * form GBD_WARN_PRECISION_FLOOR if three anchors left the residual above
+ * dav_tol. */
 int gbd_davidson(gbd_ctx* ctx, int b, double* psi, double* energy, gbd_dav_stats* stats);
 
 /* ------------------------------------ truncation (Sec. II.B step 3) */
@@ -317,8 +325,9 @@ int gbd_sweep(gbd_ctx* ctx, int nsweeps, int D, gbd_sweep_stats* stats);
  * (+1 right, -1 left), renormalisation, next start vector; with offload on,
  * the next needed environment is loaded and the new one saved to pinned host
  * memory asynchronously (Sec. III.B.4).  The position moves to b + dir.
- * Returns GBD_WARN_NOT_CONVERGED (the step still completes) when the
- * Davidson stopped at its product limit; stats->dav_status says the same. */
+ * Returns the Davidson's warning (the step still completes):
+ * GBD_WARN_NOT_CONVERGED at its product limit, GBD_WARN_PRECISION_FLOOR at
+ * the mixed form's anchor limit; stats->dav_status says the same. */
 int gbd_step(gbd_ctx* ctx, int b, int dir, int D, gbd_step_stats* stats);
 
 /* Copies the current two-site vector (position *b, sector-major layout) to
@@ -425,6 +434,10 @@ typedef struct {
     unsigned long long key;
 } gbd_tune_info;
 int gbd_tune_info_get(gbd_ctx* ctx, gbd_tune_info* out);
+
+/* Forgets every cached autotuner choice (the cache is shared by all contexts
+ * of the process); the next position of each key tries the candidates again. */
+int gbd_tune_reset(void);
 
 /* Accumulated phase timers of the context in ms, in this order: enlargement
  * planning (host), enlargement kernels, renormalisation planning (host),

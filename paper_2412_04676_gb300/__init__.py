@@ -21,7 +21,7 @@ FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK = 0, 1, 2, 3
 FAULT_PINNED_ALLOC, FAULT_IO_NEVER_READY, FAULT_CORRUPT_HOST_COPY = 1, 2, 4
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
-WARN_NOT_CONVERGED = 1
+WARN_NOT_CONVERGED, WARN_PRECISION_FLOOR = 1, 2
 
 
 class GbdError(RuntimeError):
@@ -118,9 +118,15 @@ _SIGS = {
                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gbd_timers": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     "gbd_tune_info_get": (C.c_int, [_P, C.POINTER(TuneInfo)]),
+    "gbd_tune_reset": (C.c_int, []),
     "gbd_pack_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int, _P, C.c_int, _P, _P, C.c_size_t,
                                    C.POINTER(C.c_size_t), _P]),
 }
+
+
+def tune_reset():
+    """Forget every cached autotuner choice (shared by all contexts of the process)."""
+    _check(lib().gbd_tune_reset())
 
 
 def launch_count():

@@ -443,6 +443,13 @@ int gbd_tune_info_get(gbd_ctx* c, gbd_tune_info* out) {
     });
 }
 
+int gbd_tune_reset(void) {
+    return guard([&] {
+        tc_tune_reset();
+        return GBD_OK;
+    });
+}
+
 int gbd_timers(gbd_ctx* c, double* out, int cap, int* n) {
     return guard([&] {
         Ctx& C = ctx(c);

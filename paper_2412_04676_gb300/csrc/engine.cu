@@ -1335,7 +1335,11 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             axpby(x, r, n, -theta, 1.0, s);
             dots(r, 1, r, d);
             rn = std::sqrt(std::max(0.0, d[0]));
-            if (rn <= C.cfg.dav_tol || anchors >= 3) break;
+            if (rn <= C.cfg.dav_tol) break;
+            if (anchors >= 3) {  // the mixed products' rounding floor: more anchors do not help
+                status = GBD_WARN_PRECISION_FLOOR;
+                break;
+            }
             if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
             // restart from the exact pair (x, H x)
             GBD_CHECK_CUDA(cudaMemcpyAsync(V, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -1336,6 +1336,11 @@ void tc_tune_step(Ctx& C, double ms) {
     C.timers[Ctx::T_TC_ISSUE2] = C.H.tc.pl[0].issued_p2;
 }
 
+void tc_tune_reset() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+}
+
 void tc_tune_info(Ctx& C, gbd_tune_info* out) {
     // the current position's state while it has one, else the last finished choice
     const bool cur = C.H.tc_ready && C.H.tc.tune.key != 0;

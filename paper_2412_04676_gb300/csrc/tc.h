@@ -154,6 +154,7 @@ void tc_prepare(Ctx& C, int mode);
 void tc_release_products(Ctx& C);
 void tc_tune_step(Ctx& C, double ms);       // after each BF16x3 product
 void tc_tune_info(Ctx& C, gbd_tune_info* out);
+void tc_tune_reset();                       // forgets every cached choice
 void tc_apply(Ctx& C, int mode);
 int tc_error(Ctx& C);
 bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std::vector<long long>& toff, double* tmp);

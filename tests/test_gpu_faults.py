@@ -75,3 +75,25 @@ def test_davidson_product_limit_is_a_warning():
     s = c.step(b, 1, D)
     assert s["dav_status"] == g.WARN_NOT_CONVERGED
     c.close()
+
+
+def test_mixed_davidson_reports_its_precision_floor():
+    # a tolerance below what BF16x3 products can resolve: after three anchors
+    # the mixed Davidson stops and says so (the energy is the last anchor's)
+    L, N, D, b = 8, 8, 24, 3
+    h, eri = inputs.make_integrals(L, 45)
+    sites, dims = inputs.make_mps(L, N, 0, D, 46, n_left=b)
+    c = g.Context(L, N, 0, D=D, precision=g.MIXED_BF16X3, dav_tol=1e-15, dav_max_matvec=2000)
+    c.load_integrals(h, eri)
+    c.import_mps(sites, [0] * b + [1] * (L - b))
+    c.build_envs(b)
+    e, _, st, rc = c.davidson(b)
+    assert rc == g.WARN_PRECISION_FLOOR and st["resid"] > 1e-15 and st["matvecs"] < 2000
+    ref = g.Context(L, N, 0, D=D, dav_tol=1e-11)
+    ref.load_integrals(h, eri)
+    ref.import_mps(sites, [0] * b + [1] * (L - b))
+    ref.build_envs(b)
+    e64, _, _, rc64 = ref.davidson(b)
+    assert rc64 == 0 and abs(e - e64) < 1e-8
+    c.close()
+    ref.close()

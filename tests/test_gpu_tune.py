@@ -24,8 +24,8 @@ def built():
 
 
 def test_tuner_tries_every_candidate_then_keeps_the_fastest():
-    # D=190 at L=10: a sector-size histogram no other test produces (the
-    # tuner's cache lives as long as the process)
+    # the tuner's cache is shared by every context of the process: start empty
+    g.tune_reset()
     L, N, tsz, D, b = 10, 10, 0, 190, 4
     c = heff_case(L, N, tsz, D, 700, b, oracle=False)
     ctx = c["ctx"]
