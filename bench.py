@@ -303,7 +303,7 @@ def config3_probe(device, max_matvec):
            "device_memory_model_gb": {k: info[k] / 1e9 for k in ("mem_operators", "mem_planes_bf16x3",
                                                                  "mem_planes_sliced", "mem_x_fp64", "mem_x_tensor")},
            "davidson": {"energy": e, "status": rc, "matvecs": st["matvecs"], "resid": st["resid"],
-                        "ms_products": st["ms_matvec"]},
+                        "anchor_resid": st["anchor_resid"][:st["anchors"]], "ms_products": st["ms_matvec"]},
            "bf16x3_products": int(n_bf), "bf16x3_ms_per_product": ms_bf / max(n_bf, 1),
            "bf16x3_useful_tflops": info["useful_flops"] * n_bf / (ms_bf * 1e-3) / 1e12 if ms_bf else None,
            "sliced_ms_per_product": (tm1["products_sliced_ms"] - tm0["products_sliced_ms"])
@@ -638,7 +638,9 @@ def run_ours(args, rank, world, local_rank):
                      "status_note": "0: residual <= tol; 1: product limit; 2: mixed form stopped after three "
                                     "anchors above tol (its rounding floor)",
                      "status_per_step": status, "matvecs_per_step": [s["matvecs"] for s in stats],
-                     "resid_per_step": [s["resid"] for s in stats], "max_matvec": args.max_matvec,
+                     "resid_per_step": [s["resid"] for s in stats],
+                     "anchor_resid_per_step": [s["anchor_resid"][:s["anchors"]] for s in stats],
+                     "max_matvec": args.max_matvec,
                      "tol": args.tol},
         "host_link": link,
         "fp64_compare": fp64cmp,

@@ -194,6 +194,8 @@ typedef struct {
     int matvecs;
     int iterations;
     double ms_matvec;       /* device time spent in H_eff products               */
+    int anchors;            /* mixed form: accurate anchor products taken        */
+    double anchor_resid[3]; /* exact residual norm after each anchor            */
 } gbd_dav_stats;
 
 typedef struct {
@@ -231,6 +233,8 @@ typedef struct {
                                it stopped at its product limit;
                                GBD_WARN_PRECISION_FLOOR: the mixed form's
                                anchors stopped above dav_tol                */
+    int anchors;            /* mixed form: anchor products of the Davidson      */
+    double anchor_resid[3]; /* exact residual norm after each anchor            */
 } gbd_step_stats;
 
 /* ---------------------------------------------------------------- lifecycle */

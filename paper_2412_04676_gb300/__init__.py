@@ -57,7 +57,7 @@ class StepStats(C.Structure):
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("ms_davidson", C.c_double),
                 ("ms_truncate", C.c_double), ("ms_renorm", C.c_double), ("ms_io_exposed", C.c_double),
                 ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double),
-                ("dav_status", C.c_int)]
+                ("dav_status", C.c_int), ("anchors", C.c_int), ("anchor_resid", C.c_double * 3)]
 
 
 class TuneInfo(C.Structure):
@@ -69,7 +69,7 @@ class TuneInfo(C.Structure):
 
 class DavStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int), ("iterations", C.c_int),
-                ("ms_matvec", C.c_double)]
+                ("ms_matvec", C.c_double), ("anchors", C.c_int), ("anchor_resid", C.c_double * 3)]
 
 
 class SweepStats(C.Structure):
@@ -343,7 +343,9 @@ class Context:
             psi = np.ascontiguousarray(psi, dtype=np.float64)
             p = _ptr(psi)
         rc = _check(lib().gbd_davidson(self.h, b, p, C.byref(e), C.byref(st)))
-        return e.value, psi, {k: getattr(st, k) for k, _ in DavStats._fields_}, rc
+        out = {k: getattr(st, k) for k, _ in DavStats._fields_}
+        out["anchor_resid"] = list(st.anchor_resid)
+        return e.value, psi, out, rc
 
     def truncate(self, b, direction, Dmax):
         w = C.c_double()
@@ -359,7 +361,9 @@ class Context:
         """One two-site iteration; 'dav_status' is 1 when Davidson stopped at its product limit."""
         st = StepStats()
         _check(lib().gbd_step(self.h, b, direction, D, C.byref(st)))
-        return {k: getattr(st, k) for k, _ in StepStats._fields_}
+        out = {k: getattr(st, k) for k, _ in StepStats._fields_}
+        out["anchor_resid"] = list(st.anchor_resid)
+        return out
 
     def get_psi(self, out=None):
         n = C.c_longlong()

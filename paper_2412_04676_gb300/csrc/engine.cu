@@ -1275,6 +1275,10 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     std::vector<double> w, S;
     std::vector<double> hist;  // residual norms, for the mixed-precision stagnation test
     int anchors = 0;
+    double anchor_rn[3] = {0.0, 0.0, 0.0};
+    // the anchored pair with the smallest exact residual (a later anchor can
+    // come out worse once the mixed products' rounding floor is reached)
+    double best_rn = -1.0, best_theta = 0.0;
     int status = GBD_OK;
     while (true) {
         ++iters;
@@ -1335,7 +1339,14 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             axpby(x, r, n, -theta, 1.0, s);
             dots(r, 1, r, d);
             rn = std::sqrt(std::max(0.0, d[0]));
+            anchor_rn[std::min(anchors, 3) - 1] = rn;
             if (rn <= C.cfg.dav_tol) break;
+            if (best_rn < 0.0 || rn < best_rn) {
+                C.dav_best.ensure(size_t(n) * sizeof(double));
+                GBD_CHECK_CUDA(cudaMemcpyAsync(C.dav_best.p, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                best_rn = rn;
+                best_theta = theta;
+            }
             if (anchors >= 3) {  // the mixed products' rounding floor: more anchors do not help
                 status = GBD_WARN_PRECISION_FLOOR;
                 break;
@@ -1404,6 +1415,17 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         }
         ++k;
     }
+    // a mixed Davidson that stopped on a warning returns its best anchored
+    // pair (exact Rayleigh quotient, smallest exact residual) unless the
+    // current pair is an anchored one at least as good
+    if (prec == GBD_MIXED_BF16X3 && status != GBD_OK && best_rn >= 0.0) {
+        const bool cur_anchored = anchors > 0 && anchor_rn[std::min(anchors, 3) - 1] == rn;
+        if (!cur_anchored || best_rn < rn) {
+            GBD_CHECK_CUDA(cudaMemcpyAsync(x, C.dav_best.p, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            rn = best_rn;
+            theta = best_theta;
+        }
+    }
     // normalised Ritz vector becomes the current two-site vector
     dots(x, 1, x, d);
     scale(x, n, 1.0 / std::sqrt(d[0]), s);
@@ -1421,6 +1443,8 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         st->matvecs = nmv;
         st->iterations = iters;
         st->ms_matvec = C.ms_matvec_acc - ms_mv0;
+        st->anchors = anchors;
+        for (int i = 0; i < 3; ++i) st->anchor_resid[i] = anchor_rn[i];
     }
     return status;
 }

@@ -116,7 +116,7 @@ struct Ctx {
     GemmPlan plan_a, plan_b, plan_c;
     DevBuf scratch_w, scratch_tmp, scratch_dot, scratch_small, scratch_items, scratch_srcs, scratch_cols, scratch_coefs;
     DevBuf env_sl_w, env_sl_e, env_err;  // sliced operands of the tensor-core enlargement
-    DevBuf dav_V, dav_AV, dav_r, dav_t, dav_x, dav_ax, dav_tmp;
+    DevBuf dav_V, dav_AV, dav_r, dav_t, dav_x, dav_ax, dav_tmp, dav_best;
     DevBuf stage;  // device staging for pack/unpack through pageable memory
     // statistics
     std::vector<double> step_energy;
