@@ -49,7 +49,7 @@ METRIC = "H_eff psi useful TFLOP/s over whole two-site DMRG steps (mixed BF16x3 
 # bytes; valid only while the kernel source is the one that was measured.
 TRAFFIC = {
     # profiles/tc_gemm_bf16x3_l30_d1024.md: mean of eight products at cut 14
-    "l30_d1024": {"tc_cu": "6cabe0bc2f7e47a8", "bytes_per_product": 21.49e9,
+    "l30_d1024": {"tc_cu": "6cabe0bc2f7e47a8", "form": "two_phase", "bytes_per_product": 21.49e9,
                   "source": "profiles/tc_gemm_bf16x3_l30_d1024.md (ncu, full-size workload, one-pass metrics)"},
 }
 
@@ -362,7 +362,7 @@ def run_ours(args, rank, world, local_rank):
 
     def make_ctx():
         c = g.Context(L, N, tsz, D=D, precision=prec, offload=not args.no_offload, device=local_rank,
-                      dav_tol=args.tol, dav_max_matvec=args.max_matvec)
+                      dav_tol=args.tol, dav_max_matvec=args.max_matvec, bf16x3_fused=not args.two_phase)
         c.load_integrals(h, eri)
         c.import_mps(sites, [0] * b + [1] * (L - b))
         c.build_envs(b)
@@ -468,6 +468,19 @@ def run_ours(args, rank, world, local_rank):
             y64 = ctx.apply_heff(pb_c, xg, precision=g.FP64)
             ypb = ctx.apply_heff(pb_c, xg, precision=g.FP64_PER_BLOCK)
             tq1 = ctx.timers()
+            # the two BF16x3 kernel forms on the same vector: the context's
+            # (fused unless --two-phase) against the two-kernel form, three
+            # products each after one that builds the plan
+            forms_ms = {}
+            for name, code, key in (("two_phase", g.BF16X3_TWO_PHASE, "products_bf16x3_two_phase"),
+                                    ("context", g.MIXED_BF16X3, "products_bf16x3")):
+                ctx.apply_heff(pb_c, xg, precision=code)
+                ta = ctx.timers()
+                for _ in range(3):
+                    yk = ctx.apply_heff(pb_c, xg, precision=code)
+                tb = ctx.timers()
+                forms_ms[name] = {"ms_per_product": (tb[key + "_ms"] - ta[key + "_ms"]) / 3,
+                                  "rel_resid": float(torch.linalg.norm(yk - y64)) / float(torch.linalg.norm(y64))}
             n64 = float(torch.linalg.norm(y64))
             e64, em, es = float(xg @ y64), float(xg @ ym), float(xg @ ys)
             fp64cmp = {"position": pb_c, "rel_resid_bf16x3": float(torch.linalg.norm(ym - y64)) / n64,
@@ -477,6 +490,7 @@ def run_ours(args, rank, world, local_rank):
                        "ms_fp64_per_block_product": tq1["products_fp64_per_block_ms"]
                                                     - tq0["products_fp64_per_block_ms"],
                        "per_block_bitwise_equal": bool(torch.equal(ypb, y64)),
+                       "bf16x3_kernel_forms": dict(forms_ms, context_form="two_phase" if args.two_phase else "fused"),
                        "note": "one product of each form on the current two-site vector; the mixed Davidson's "
                                "energy comes from sliced anchor products (abs_dE_sliced)"}
         except Exception as e:  # measurement extra; never fatal
@@ -556,13 +570,16 @@ def run_ours(args, rank, world, local_rank):
         peak = bf16_sust / 3.0
         tr = TRAFFIC.get(args.workload)
         traffic = None
-        if tr and tr.get("tc_cu") == src_hash("paper_2412_04676_gb300/csrc/tc.cu"):
+        if (tr and tr.get("tc_cu") == src_hash("paper_2412_04676_gb300/csrc/tc.cu")
+                and tr.get("form") == ("two_phase" if args.two_phase else "fused")):
             traffic = tr["bytes_per_product"]
         roofs["bf16x3"] = {
             "bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
             "traffic": traffic, "traffic_source": tr["source"] if traffic else "no capture of this kernel build",
             "ms": f["ms"], "launches": n,
-            "kernel": "tc_gemm_kernel<0, 1> + <0, 2> (+ split, reduce): BF16x3 H_eff product",
+            "kernel": ("tc_gemm_kernel<0, 1> + <0, 2> (+ split, reduce): BF16x3 H_eff product in two kernels"
+                       if args.two_phase else
+                       "tc_fused_kernel (+ split, reduce): BF16x3 H_eff product, X kept in TMEM"),
             "peak_source": f"{peak_src}: bf16 sustained / 3 (three split products per useful flop; "
                            "the product is timed inside whole steps)",
             "algorithmic_bytes_per_product": gb / n * 1e9,
@@ -570,7 +587,8 @@ def run_ours(args, rank, world, local_rank):
             "hbm_view": {"achieved": gb / (f["ms"] * 1e-3), "peak": hbm, "unit": "GB/s",
                          "frac": gb / (f["ms"] * 1e-3) / hbm, "peak_source": f"{peak_src}: HBM copy bandwidth"},
             "x_overhead_bytes_per_product": xgb / n * 1e9,
-            "x_overhead_note": "phase-1 intermediate X written and read once (BF16 hi+lo), not algorithmic",
+            "x_overhead_note": "two-kernel form: phase-1 intermediate X written and read once (BF16 hi+lo), "
+                               "not algorithmic; 0 for the fused kernel",
             "intensity_flop_per_byte": 3.0 * f["useful_gflop"] / gb if gb else None,
             "ridge_flop_per_byte": bf16_sust * 1e3 / hbm,
             "issued_tflops": (dt["tc_issued_gflop_p1"] + dt["tc_issued_gflop_p2"]) * n / f["ms"],
@@ -635,8 +653,9 @@ def run_ours(args, rank, world, local_rank):
         "davidson": {"converged_steps": sum(1 for x in status if x == 0), "steps": len(status),
                      "at_product_limit": sum(1 for x in status if x == 1),
                      "at_precision_floor": sum(1 for x in status if x == 2),
-                     "status_note": "0: residual <= tol; 1: product limit; 2: mixed form stopped after three "
-                                    "anchors above tol (its rounding floor)",
+                     "status_note": "0: residual <= tol; 1: product limit; 2: mixed form stopped at its "
+                                    "rounding floor (an anchor that did not halve the exact residual, or six "
+                                    "anchors) above tol",
                      "status_per_step": status, "matvecs_per_step": [s["matvecs"] for s in stats],
                      "resid_per_step": [s["resid"] for s in stats],
                      "anchor_resid_per_step": [s["anchor_resid"][:s["anchors"]] for s in stats],
@@ -674,6 +693,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-offload", action="store_true")
+    ap.add_argument("--two-phase", action="store_true",
+                    help="BF16x3 products in two kernels with X in HBM (default: the fused kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tol", type=float, default=1e-6)

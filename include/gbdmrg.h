@@ -58,11 +58,16 @@ enum {
     GBD_ERR_CORRUPT = -6,      /* package magic / checksum / metadata mismatch   */
     GBD_ERR_STATE = -7,        /* call out of order (e.g. no integrals loaded)   */
     GBD_WARN_NOT_CONVERGED = 1, /* Davidson hit its product limit                */
-    GBD_WARN_PRECISION_FLOOR = 2 /* mixed Davidson: after three anchors the exact
-                                    residual is still above dav_tol (the floor
-                                    the BF16x3 products leave); the energy is the
-                                    last anchor's Rayleigh quotient            */
+    GBD_WARN_PRECISION_FLOOR = 2 /* mixed Davidson: its anchors stopped above
+                                    dav_tol (an anchor that did not halve the
+                                    best exact residual, or GBD_MAX_ANCHORS of
+                                    them: the floor the BF16x3 products leave);
+                                    the result is the anchored pair with the
+                                    smallest exact residual                    */
 };
+
+/* Most accurate anchor products of one mixed Davidson solve. */
+#define GBD_MAX_ANCHORS 6
 
 /* H_eff product forms.  GBD_FP64: FP64 GEMMs.  GBD_MIXED_BF16X3: every
  * operand split elementwise into BF16 hi + lo, products hh + hl + lh on the
@@ -74,10 +79,13 @@ enum {
  * 2^-30 relative to the row maxima).  GBD_SLICED_BF16 is a product form for
  * gbd_apply_heff and for Davidson anchors (mixed_polish = 2), not a
  * context precision. */
-enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2, GBD_FP64_PER_BLOCK = 3 };
+enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2, GBD_FP64_PER_BLOCK = 3, GBD_BF16X3_TWO_PHASE = 4 };
 /* GBD_FP64_PER_BLOCK: the FP64 product with one kernel launch per sector
  * block GEMM task instead of one grouped launch per phase (same kernel, same
- * tiles, bitwise the same result); a comparison form for gbd_apply_heff. */
+ * tiles, bitwise the same result); a comparison form for gbd_apply_heff.
+ * GBD_BF16X3_TWO_PHASE: the BF16x3 product in two kernels with X stored in
+ * HBM between them, whatever gbd_config.bf16x3_fused says (same split
+ * products, another summation order); a comparison form for gbd_apply_heff. */
 
 typedef struct gbd_ctx gbd_ctx;
 
@@ -145,6 +153,12 @@ typedef struct {
                            buffer would not fit beside them; 1: always;
                            -1: never.  A later GBD_FP64 product at the same
                            position enlarges the operators again.          */
+    int bf16x3_fused;   /* BF16x3 products: 1 (default) one fused kernel per
+                           product (each chunk of X = O^Lx psi is formed in
+                           tensor memory, split into BF16 hi / lo there and
+                           multiplied at once into the output tile, so X
+                           never reaches HBM); 0: two kernels with X stored
+                           in HBM between them                             */
 } gbd_config;
 
 /* Host-side fault injection (gbd_config.fault_inject).  Each failure is made
@@ -195,7 +209,7 @@ typedef struct {
     int iterations;
     double ms_matvec;       /* device time spent in H_eff products               */
     int anchors;            /* mixed form: accurate anchor products taken        */
-    double anchor_resid[3]; /* exact residual norm after each anchor            */
+    double anchor_resid[GBD_MAX_ANCHORS]; /* exact residual norm after each anchor */
 } gbd_dav_stats;
 
 typedef struct {
@@ -234,7 +248,7 @@ typedef struct {
                                GBD_WARN_PRECISION_FLOOR: the mixed form's
                                anchors stopped above dav_tol                */
     int anchors;            /* mixed form: anchor products of the Davidson      */
-    double anchor_resid[3]; /* exact residual norm after each anchor            */
+    double anchor_resid[GBD_MAX_ANCHORS]; /* exact residual norm after each anchor */
 } gbd_step_stats;
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -293,8 +307,8 @@ int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n,
 /* psi_out = H_eff psi_in at position b (Sec. II.B step 2).  Vectors in the
  * sector-major layout above, FP64.  on_device = 1: both pointers are device
  * pointers; 0: host pointers (copied in and out).  precision selects the
- * product form (GBD_FP64, GBD_MIXED_BF16X3, GBD_SLICED_BF16 or
- * GBD_FP64_PER_BLOCK).  psi_out may not alias psi_in. */
+ * product form (GBD_FP64, GBD_MIXED_BF16X3, GBD_SLICED_BF16,
+ * GBD_FP64_PER_BLOCK or GBD_BF16X3_TWO_PHASE).  psi_out may not alias psi_in. */
 int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, int on_device, int precision);
 
 /* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
@@ -471,7 +485,8 @@ int gbd_tune_reset(void);
  * then the host wall time (ms) of environment recomputation
  * (env_recompute) and the number of environments it rebuilt, then the GB
  * written to and read back from the spill file and the host time (ms) spent
- * waiting for spill jobs (host_store_bytes).
+ * waiting for spill jobs (host_store_bytes), then the device time (ms) and
+ * number of GBD_BF16X3_TWO_PHASE products.
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

@@ -17,11 +17,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
 HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
 
-FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK = 0, 1, 2, 3
+FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK, BF16X3_TWO_PHASE = 0, 1, 2, 3, 4
 FAULT_PINNED_ALLOC, FAULT_IO_NEVER_READY, FAULT_CORRUPT_HOST_COPY = 1, 2, 4
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
 WARN_NOT_CONVERGED, WARN_PRECISION_FLOOR = 1, 2
+MAX_ANCHORS = 6  # GBD_MAX_ANCHORS
 
 
 class GbdError(RuntimeError):
@@ -37,7 +38,7 @@ class Config(C.Structure):
                 ("switch_cut", C.c_int), ("io_timeout_ms", C.c_int), ("seed", C.c_ulonglong),
                 ("mixed_fp64_blocks", C.c_int), ("mixed_polish", C.c_int), ("fault_inject", C.c_int),
                 ("autotune", C.c_int), ("env_recompute", C.c_int), ("host_store_bytes", C.c_longlong),
-                ("low_memory", C.c_int)]
+                ("low_memory", C.c_int), ("bf16x3_fused", C.c_int)]
 
 
 class SectorInfo(C.Structure):
@@ -57,7 +58,7 @@ class StepStats(C.Structure):
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("ms_davidson", C.c_double),
                 ("ms_truncate", C.c_double), ("ms_renorm", C.c_double), ("ms_io_exposed", C.c_double),
                 ("useful_flops", C.c_double), ("bytes_packed", C.c_double), ("ms_device", C.c_double),
-                ("dav_status", C.c_int), ("anchors", C.c_int), ("anchor_resid", C.c_double * 3)]
+                ("dav_status", C.c_int), ("anchors", C.c_int), ("anchor_resid", C.c_double * MAX_ANCHORS)]
 
 
 class TuneInfo(C.Structure):
@@ -69,7 +70,7 @@ class TuneInfo(C.Structure):
 
 class DavStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("resid", C.c_double), ("matvecs", C.c_int), ("iterations", C.c_int),
-                ("ms_matvec", C.c_double), ("anchors", C.c_int), ("anchor_resid", C.c_double * 3)]
+                ("ms_matvec", C.c_double), ("anchors", C.c_int), ("anchor_resid", C.c_double * MAX_ANCHORS)]
 
 
 class SweepStats(C.Structure):
@@ -245,7 +246,7 @@ class Context:
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
                  mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0, autotune=True,
-                 env_recompute=0, host_store_bytes=0):
+                 env_recompute=0, host_store_bytes=0, bf16x3_fused=True):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -258,6 +259,7 @@ class Context:
         cfg.autotune = int(autotune)
         cfg.env_recompute = int(env_recompute)
         cfg.host_store_bytes = int(host_store_bytes)
+        cfg.bf16x3_fused = int(bf16x3_fused)
         h = C.c_void_p()
         _check(lib().gbd_create(C.byref(cfg), C.byref(h)))
         self.h = h
@@ -429,7 +431,7 @@ class Context:
               "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
               "products_bf16x3_gbytes", "products_bf16x3_x_gbytes", "products_fp64_per_block_ms",
               "products_fp64_per_block_n", "recompute_ms", "recompute_n", "spill_gbytes", "restore_gbytes",
-              "spill_wait_ms"]
+              "spill_wait_ms", "products_bf16x3_two_phase_ms", "products_bf16x3_two_phase_n"]
 
     def timers(self):
         out = np.zeros(64)

@@ -68,6 +68,7 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->autotune = 1;
     cfg->env_recompute = 0;
     cfg->host_store_bytes = 0;
+    cfg->bf16x3_fused = 1;
     return GBD_OK;
 }
 
@@ -88,6 +89,7 @@ int gbd_create(const gbd_config* cfg, gbd_ctx** out) {
         GBD_REQUIRE(cfg->autotune == 0 || cfg->autotune == 1, GBD_ERR_ARG, "autotune must be 0 or 1");
         GBD_REQUIRE(cfg->env_recompute == 0 || cfg->env_recompute >= 2, GBD_ERR_ARG, "env_recompute must be 0 or >= 2");
         GBD_REQUIRE(cfg->host_store_bytes >= 0, GBD_ERR_ARG, "host_store_bytes must be >= 0");
+        GBD_REQUIRE(cfg->bf16x3_fused == 0 || cfg->bf16x3_fused == 1, GBD_ERR_ARG, "bf16x3_fused must be 0 or 1");
         auto* c = new gbd_ctx();
         c->C.cfg = *cfg;
         *out = c;
@@ -217,7 +219,7 @@ int gbd_apply_heff(gbd_ctx* c, int b, const double* psi_in, double* psi_out, int
         Ctx& C = ctx(c);
         GBD_REQUIRE(psi_in && psi_out && psi_in != psi_out, GBD_ERR_ARG, "bad vectors");
         GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 ||
-                        precision == GBD_FP64_PER_BLOCK, GBD_ERR_ARG,
+                        precision == GBD_FP64_PER_BLOCK || precision == GBD_BF16X3_TWO_PHASE, GBD_ERR_ARG,
                     "bad precision");
         ensure_heff(C, b);
         Heff& H = C.H;

@@ -1057,9 +1057,14 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     Heff& H = C.H;
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
-    const bool tensor = precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16;
+    const bool two = precision == GBD_BF16X3_TWO_PHASE;
+    const bool tensor = precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 || two;
     const int mode = precision == GBD_SLICED_BF16 ? 1 : 0;
     if (tensor) {
+        // the BF16x3 plan is fused or two-phase: a request for the other form re-plans it
+        if (mode == 0 && H.tc_ready && H.tc.pl[0].built && H.tc.pl[0].fused == (two || !C.cfg.bf16x3_fused))
+            H.tc.pl[0].built = false;
+        if (mode == 0) H.tc.two_phase = two;
         if (!H.tc_ready || !H.tc.pl[mode].built) {
             const double tt0 = wall_ms();
             tc_prepare(C, mode);
@@ -1094,6 +1099,9 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     if (precision == GBD_FP64_PER_BLOCK) {
         C.timers[Ctx::T_PROD_MS_PB] += ms;
         C.timers[Ctx::T_PROD_N_PB] += 1.0;
+    } else if (two) {
+        C.timers[Ctx::T_PROD_MS_TP] += ms;
+        C.timers[Ctx::T_PROD_N_TP] += 1.0;
     } else {
         C.timers[Ctx::T_PROD_MS0 + precision] += ms;
         C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
@@ -1101,7 +1109,7 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     }
     if (precision == GBD_MIXED_BF16X3) {
         C.timers[Ctx::T_PROD_GB1] += H.mixed_bytes * 1e-9;
-        C.timers[Ctx::T_PROD_XGB1] += H.mixed_x_bytes * 1e-9;
+        if (!H.tc.pl[0].fused) C.timers[Ctx::T_PROD_XGB1] += H.mixed_x_bytes * 1e-9;  // the fused kernel keeps X on the SM
         tc_tune_step(C, ms);
     }
 }
@@ -1198,7 +1206,9 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     const int prec = C.cfg.precision;
     // a BF16x3 product carries ~1e-5 relative rounding, so its residual cannot
     // fall much below that; the anchor products (below) fix the energy
-    const double tol = prec == GBD_MIXED_BF16X3 ? std::max(C.cfg.dav_tol, 2e-5) : C.cfg.dav_tol;
+    // (after the first anchor the subspace holds an exact pair and the
+    // residual estimate follows the exact one down to dav_tol)
+    double tol = prec == GBD_MIXED_BF16X3 ? std::max(C.cfg.dav_tol, 2e-5) : C.cfg.dav_tol;
     heff_diag(C);
     C.dav_V.ensure(size_t(kmax) * n * sizeof(double));
     C.dav_AV.ensure(size_t(kmax) * n * sizeof(double));
@@ -1268,6 +1278,16 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         apply_heff_dev(C, V, AV, prec);
     }
     int nmv = 1, k = 1, iters = 0;
+    // exact0: column 0 of AV is an accurate product (the exact start, or the
+    // anchored pair after a restart).  H is symmetric, so the projections of
+    // later columns onto it are taken on its accurate side, (H x) . v,
+    // instead of x . (H v) with v's mixed product: only the block of the
+    // correction directions then carries the mixed products' rounding, and
+    // each anchor round shrinks the exact residual instead of converging
+    // back to the mixed operator's eigenvector.  A full subspace then
+    // restarts through an anchor (not a thick restart, whose kept vectors
+    // would mix accurate and mixed products).
+    bool exact0 = exact_start;
     std::vector<double> Hs(size_t(kmax) * kmax, 0.0);
     dots(V, 1, AV, d);
     Hs[0] = d[0];
@@ -1275,7 +1295,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     std::vector<double> w, S;
     std::vector<double> hist;  // residual norms, for the mixed-precision stagnation test
     int anchors = 0;
-    double anchor_rn[3] = {0.0, 0.0, 0.0};
+    double anchor_rn[GBD_MAX_ANCHORS] = {0.0};
     // the anchored pair with the smallest exact residual (a later anchor can
     // come out worse once the mixed products' rounding floor is reached)
     double best_rn = -1.0, best_theta = 0.0;
@@ -1300,11 +1320,11 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         if (prec == GBD_MIXED_BF16X3 && C.cfg.mixed_polish) {
             // Mixed products carry ~1e-5 relative noise, so the residual stalls
             // at a floor that grows with |theta|.  At the floor (or at the
-            // tolerance) the Ritz vector is anchored: one FP64 product gives
-            // its exact residual; if that is below the tolerance we are done,
-            // otherwise the subspace restarts from the exact pair and further
-            // mixed directions only correct it, which shrinks the error by
-            // about the products' relative accuracy per round.
+            // tolerance) the Ritz vector is anchored: one accurate product
+            // (sliced or FP64) gives its exact residual; if that is below the
+            // tolerance we are done, otherwise the subspace restarts from the
+            // exact pair and further mixed directions only correct it (exact0
+            // below), which shrinks the exact residual round by round.
             hist.push_back(rn);
             bool stalled = false;
             if (hist.size() > 9) {
@@ -1314,7 +1334,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
                 // < 10% gain in 6 iterations, near the mixed floor (~1e-5 |theta|)
                 stalled = recent > 0.9 * before && rn <= 1e-4 * std::max(1.0, std::fabs(theta));
             }
-            anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec;
+            anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec || (exact0 && k >= kmax);
             if (k == 1 && exact_start && anchors == 0 && iters == 1) {
                 // the residual of the start vector is already exact
                 if (rn <= C.cfg.dav_tol) break;
@@ -1339,18 +1359,22 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             axpby(x, r, n, -theta, 1.0, s);
             dots(r, 1, r, d);
             rn = std::sqrt(std::max(0.0, d[0]));
-            anchor_rn[std::min(anchors, 3) - 1] = rn;
+            anchor_rn[std::min(anchors, GBD_MAX_ANCHORS) - 1] = rn;
             if (rn <= C.cfg.dav_tol) break;
+            const double prev_best = best_rn;
             if (best_rn < 0.0 || rn < best_rn) {
                 C.dav_best.ensure(size_t(n) * sizeof(double));
                 GBD_CHECK_CUDA(cudaMemcpyAsync(C.dav_best.p, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 best_rn = rn;
                 best_theta = theta;
             }
-            if (anchors >= 3) {  // the mixed products' rounding floor: more anchors do not help
+            // the mixed products' rounding floor: an anchor round that does not
+            // halve the best exact residual, or the last allowed anchor
+            if (anchors >= GBD_MAX_ANCHORS || (prev_best >= 0.0 && rn > 0.5 * prev_best)) {
                 status = GBD_WARN_PRECISION_FLOOR;
                 break;
             }
+            tol = C.cfg.dav_tol;
             if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
             // restart from the exact pair (x, H x)
             GBD_CHECK_CUDA(cudaMemcpyAsync(V, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1358,6 +1382,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             std::fill(Hs.begin(), Hs.end(), 0.0);
             Hs[0] = theta;
             k = 1;
+            exact0 = true;
             hist.clear();
         }
         if (nmv >= C.cfg.dav_max_matvec) { status = GBD_WARN_NOT_CONVERGED; break; }
@@ -1400,6 +1425,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
             std::fill(Hs.begin(), Hs.end(), 0.0);
             for (int j = 0; j < keep; ++j) Hs[j * kmax + j] = w[j];
             k = keep;
+            exact0 = false;
             orth(k);
             dots(t, 1, t, d);
             scale(t, n, 1.0 / std::sqrt(std::max(d[0], 1e-300)), s);
@@ -1409,6 +1435,10 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         ++nmv;
         std::vector<double> hcol;
         dots(V, k + 1, AV + size_t(k) * n, hcol);
+        if (exact0 && prec == GBD_MIXED_BF16X3) {
+            dots(AV, 1, V + size_t(k) * n, d);  // (H x) . v on the accurate side
+            hcol[0] = d[0];
+        }
         for (int i = 0; i <= k; ++i) {
             Hs[i * kmax + k] = hcol[i];
             Hs[k * kmax + i] = hcol[i];
@@ -1419,7 +1449,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
     // pair (exact Rayleigh quotient, smallest exact residual) unless the
     // current pair is an anchored one at least as good
     if (prec == GBD_MIXED_BF16X3 && status != GBD_OK && best_rn >= 0.0) {
-        const bool cur_anchored = anchors > 0 && anchor_rn[std::min(anchors, 3) - 1] == rn;
+        const bool cur_anchored = anchors > 0 && anchor_rn[std::min(anchors, GBD_MAX_ANCHORS) - 1] == rn;
         if (!cur_anchored || best_rn < rn) {
             GBD_CHECK_CUDA(cudaMemcpyAsync(x, C.dav_best.p, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
             rn = best_rn;
@@ -1444,7 +1474,7 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         st->iterations = iters;
         st->ms_matvec = C.ms_matvec_acc - ms_mv0;
         st->anchors = anchors;
-        for (int i = 0; i < 3; ++i) st->anchor_resid[i] = anchor_rn[i];
+        for (int i = 0; i < GBD_MAX_ANCHORS; ++i) st->anchor_resid[i] = anchor_rn[i];
     }
     return status;
 }

@@ -683,7 +683,7 @@ int run_step(Ctx& C, int b, int dir, int D, gbd_step_stats* out) {
         out->bytes_packed = C.io_d2h - d2h0;
         out->dav_status = dav_status;
         out->anchors = ds.anchors;
-        for (int i = 0; i < 3; ++i) out->anchor_resid[i] = ds.anchor_resid[i];
+        for (int i = 0; i < GBD_MAX_ANCHORS; ++i) out->anchor_resid[i] = ds.anchor_resid[i];
     }
     return dav_status;
 }

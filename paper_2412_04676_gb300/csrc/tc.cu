@@ -17,6 +17,9 @@
 // fill of TMA boxes handles ragged sector edges.  Every spin-wait is
 // bounded: on expiry the CTA records an error code in a device word, stops
 // issuing, waits (bounded) for its copies and frees TMEM.
+// The BF16x3 product also runs as one fused kernel (tc_fused_kernel, the
+// default): each chunk of X is formed in TMEM, split there and multiplied
+// into the output tile at once, so X never reaches HBM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -582,6 +585,375 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     }
 }
 
+// ------------------------------------------------------------------ the fused BF16x3 product
+// One kernel for both phases of the BF16x3 product.  A work item is an output
+// tile (128 rows of the output left sector x up to 256 columns of the output
+// right sector) and a range of chunks of its segments (FSeg).  Per chunk:
+//   P1: Xacc (TMEM, FP32) = O^Lx_t[tile rows, :] psi[:, FN columns]   (K = mLi)
+//   split: the epilogue warps read Xacc, split it into BF16 hi / lo and store
+//          both back into TMEM, where the next MMAs take them as operand A;
+//   P2: Y (TMEM, FP32) += X_t(hi, lo) O^xR_t[tile columns, FN columns]^T (K = FN)
+// Xacc and the split X are double-buffered and the MMA thread issues P1 of
+// chunk g before P2 of chunk g - 1, so the tensor pipe runs P1(g) while the
+// epilogue splits chunk g - 1 and never waits for a split younger than one
+// chunk.  Operands come through one TMA ring of 64 KB stages in the MMA
+// thread's consumption order (the P1 stages of chunk g, then the P2 stage of
+// chunk g - 1).  At the end of an item the epilogue drains Y into an FP32
+// split-K partial tile (the layout of the two-kernel form's partials, summed
+// by reduce_kernel).
+// TMEM columns: Y 0-255; buffer b: Xacc 256 + 64 b, X hi 384 + 64 b, X lo
+// 416 + 64 b (two BF16 per 32-bit column).  Every wait is bounded; on expiry
+// the CTA records an error code, stops, waits (bounded) for its copies and
+// MMAs, frees TMEM.
+
+// Chunks of one fused split-K item: its FP32 sum in TMEM runs over at most
+// 32 * FN = 2048 terms of K per output element (3 * 128 accumulation steps
+// of K = 16, each rounded to FP32).
+constexpr int kFusedChunks = 32;
+
+struct KF {
+    static constexpr int BN = 256;                // output tile columns
+    static constexpr int STAGES = 3;
+    static constexpr int PL = BM * BK * 2;        // one plane of an O^Lx tile: 128 rows x 64 (16 KB)
+    static constexpr int PP = FN * BK * 2;        // one plane of a psi^T tile: 64 rows x 64 (8 KB)
+    static constexpr int RPL = BN * BK * 2;       // one plane of an O^xR tile: 256 rows x 64 (32 KB)
+    static constexpr int P1_BYTES = 2 * PL + 2 * PP;  // P1 stage: O^Lx hi, lo, psi^T hi, lo
+    static constexpr int P2_BYTES = 2 * RPL;          // P2 stage: O^xR hi, lo
+    static constexpr int STAGE_BYTES = P2_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+    static constexpr uint32_t Y = 0, XACC = 256, XHI = 384, XLO = 416, XSTEP = 64, TMEM_COLS = 512;
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BM >> 4) << 24);
+    static_assert(P1_BYTES <= STAGE_BYTES, "a P1 stage fits a ring stage");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+    static_assert(FN == BK && FN == 64 && BN % 64 == 0, "one P2 stage per chunk, four epilogue column parts");
+};
+
+__device__ __forceinline__ uint32_t idesc_n(uint32_t base, int n) { return (base & ~(0x3Fu << 17)) | (uint32_t(n >> 3) << 17); }
+
+// D (TMEM) += A (TMEM, K-major, two BF16 per column) x B (shared memory descriptor)
+__device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// One chunk of the CTA's chunk stream (items blockIdx.x, + gridDim.x, ...).
+struct FChunk {
+    int wi, s, t, j0;
+    int n1;          // MMA width of the X chunk: valid columns rounded up to 16
+    int n2;          // MMA width of the output tile
+    int m0, n0;
+    int item;        // ordinal of the item within this CTA
+    bool first, last;
+};
+struct FIter {
+    int wi = -1, c = 0, c1 = 0, s = 0, t = 0, jb = 0, item = -1;
+    bool first = false;
+};
+
+// Every role walks the same stream with the same code, so the TMA ring and
+// the barriers see one order.
+__device__ __forceinline__ bool fnext(const Work* __restrict__ works, int nworks, const FSeg* __restrict__ segs, FIter& it,
+                                      FChunk& ch) {
+    while (it.c >= it.c1) {
+        it.wi = it.wi < 0 ? int(blockIdx.x) : it.wi + int(gridDim.x);
+        if (it.wi >= nworks) return false;
+        const Work& w = works[it.wi];
+        it.c = w.c0;
+        it.c1 = w.c1;
+        if (it.c >= it.c1) continue;
+        int c = it.c, s = w.seg0;
+        while (s < w.seg0 + w.nseg && c >= segs[s].nchunk) { c -= segs[s].nchunk; ++s; }
+        if (s >= w.seg0 + w.nseg) { it.c = it.c1; continue; }  // range past its segments: nothing to do
+        ++it.item;
+        it.s = s;
+        it.t = c / segs[s].ncol;
+        it.jb = c - it.t * segs[s].ncol;
+        it.first = true;
+    }
+    const Work& w = works[it.wi];
+    const FSeg& sg = segs[it.s];
+    ch.wi = it.wi;
+    ch.s = it.s;
+    ch.t = it.t;
+    ch.j0 = it.jb * FN;
+    ch.n1 = tile_n_of<FN>(sg.mRi, ch.j0);
+    ch.n2 = tile_n_of<KF::BN>(w.N, w.n0);
+    ch.m0 = w.m0;
+    ch.n0 = w.n0;
+    ch.item = it.item;
+    ch.first = it.first;
+    it.first = false;
+    ++it.c;
+    ch.last = it.c >= it.c1;
+    if (++it.jb >= sg.ncol) {
+        it.jb = 0;
+        if (++it.t >= sg.T) { it.t = 0; ++it.s; }
+    }
+    // a range that runs past its item's segments ends here
+    if (!ch.last && it.s >= w.seg0 + w.nseg) { it.c = it.c1; ch.last = true; }
+    return true;
+}
+
+__global__ void __launch_bounds__(THREADS, 1) tc_fused_kernel(const Work* __restrict__ works, int nworks,
+                                                              const FSeg* __restrict__ segs,
+                                                              const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[KF::STAGES], empty_bar[KF::STAGES];
+    __shared__ __align__(8) uint64_t xacc_full[2], xacc_free[2], xbf_full[2], xbf_free[2], y_full, y_empty, mma_done;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < KF::STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&xacc_full[b]), 1);
+            mbar_init(smem_u32(&xacc_free[b]), EPI_WARPS);
+            mbar_init(smem_u32(&xbf_full[b]), EPI_WARPS);
+            mbar_init(smem_u32(&xbf_free[b]), 1);
+        }
+        mbar_init(smem_u32(&y_full), 1);
+        mbar_init(smem_u32(&y_empty), EPI_WARPS);
+        mbar_init(smem_u32(&mma_done), 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(KF::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: P1 stages of chunk g, then the P2 stage of chunk g - 1
+        long long g = 0;  // stages issued
+        auto stage = [&](uint32_t bytes, uint32_t& bar, uint8_t*& base) -> bool {
+            const int st = int(g % KF::STAGES);
+            if (g >= KF::STAGES && !mbar_wait(smem_u32(&empty_bar[st]), uint32_t(((g / KF::STAGES) & 1) ^ 1))) {
+                atomicExch(err, 11);
+                vstore(abort_s, 1);
+                return false;
+            }
+            if (vload(abort_s)) return false;
+            bar = smem_u32(&full_bar[st]);
+            base = smem + st * KF::STAGE_BYTES;
+            mbar_expect_tx(bar, bytes);
+            ++g;
+            return true;
+        };
+        auto load_p2 = [&](const FChunk& p) -> bool {
+            uint32_t bar;
+            uint8_t* base;
+            if (!stage(KF::P2_BYTES, bar, base)) return false;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) tma_4d(smem_u32(base + q * KF::RPL), maps + segs[p.s].mapR, p.j0, p.t, p.n0, q, bar);
+            return true;
+        };
+        FIter it;
+        FChunk cur, prev;
+        bool hp = false, ok = true;
+        while (ok && fnext(works, nworks, segs, it, cur)) {
+            const FSeg& sg = segs[cur.s];
+            for (int k1 = 0; k1 < sg.nk1 && ok; ++k1) {
+                uint32_t bar;
+                uint8_t* base;
+                if (!(ok = stage(KF::P1_BYTES, bar, base))) break;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    tma_4d(smem_u32(base + q * KF::PL), maps + sg.mapL, k1 * BK, cur.m0, cur.t, q, bar);
+                    tma_3d(smem_u32(base + 2 * KF::PL + q * KF::PP), maps + sg.mapP, k1 * BK, cur.j0, q, bar);
+                }
+            }
+            if (ok && hp) ok = load_p2(prev);
+            prev = cur;
+            hp = true;
+        }
+        if (ok && hp) load_p2(prev);
+        // on abort: let the loads already issued land before the CTA may exit
+        if (vload(abort_s))
+            for (long long i = (g > KF::STAGES ? g - KF::STAGES : 0); i < g; ++i)
+                mbar_wait(smem_u32(&full_bar[i % KF::STAGES]), uint32_t((i / KF::STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        long long g = 0;  // stages consumed
+        int gc = 0;       // chunks whose P1 was issued
+        auto fail = [&](int code) {
+            atomicExch(err, code);
+            vstore(abort_s, 1);
+            return false;
+        };
+        auto take = [&](uint32_t& base) -> bool {
+            const int st = int(g % KF::STAGES);
+            if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / KF::STAGES) & 1))) return fail(12);
+            if (vload(abort_s)) return false;
+            tc_fence_after();
+            base = smem_u32(smem + st * KF::STAGE_BYTES);
+            return true;
+        };
+        auto release = [&]() { umma_commit(smem_u32(&empty_bar[int(g % KF::STAGES)])); ++g; };
+        // P2 of chunk p (the pc-th chunk of the stream)
+        auto issue_p2 = [&](const FChunk& p, int pc) -> bool {
+            const int b = pc & 1;
+            if (p.first && p.item > 0) {
+                if (!mbar_wait(smem_u32(&y_empty), uint32_t((p.item - 1) & 1))) return fail(13);
+                tc_fence_after();
+            }
+            if (!mbar_wait(smem_u32(&xbf_full[b]), uint32_t((pc >> 1) & 1))) return fail(14);
+            tc_fence_after();
+            const uint32_t idesc = idesc_n(KF::IDESC, p.n2);
+            uint32_t b0;
+            if (!take(b0)) return false;
+            const uint32_t xh = tmem + KF::XHI + b * KF::XSTEP, xl = tmem + KF::XLO + b * KF::XSTEP;
+            for (int k = 0; k < p.n1 / 16; ++k) {
+                const uint64_t bh = sdesc(b0 + k * 32), bl = sdesc(b0 + KF::RPL + k * 32);
+                const uint32_t acc = (!p.first || k > 0) ? 1u : 0u;
+                umma_ts(tmem + KF::Y, xh + k * 8, bh, idesc, acc);  // 16 BF16 of K = 8 TMEM columns
+                umma_ts(tmem + KF::Y, xh + k * 8, bl, idesc, 1u);
+                umma_ts(tmem + KF::Y, xl + k * 8, bh, idesc, 1u);
+            }
+            release();
+            umma_commit(smem_u32(&xbf_free[b]));
+            if (p.last) umma_commit(smem_u32(&y_full));
+            return true;
+        };
+        FIter it;
+        FChunk cur, prev;
+        bool hp = false, ok = true;
+        while (ok && fnext(works, nworks, segs, it, cur)) {
+            const FSeg& sg = segs[cur.s];
+            const int b = gc & 1;
+            if (gc >= 2) {
+                if (!(ok = mbar_wait(smem_u32(&xacc_free[b]), uint32_t(((gc >> 1) - 1) & 1)) || fail(15))) break;
+                tc_fence_after();
+            }
+            const uint32_t idesc = idesc_n(KF::IDESC, cur.n1);
+            const uint32_t xa = tmem + KF::XACC + b * KF::XSTEP;
+            for (int k1 = 0; k1 < sg.nk1 && ok; ++k1) {
+                uint32_t a0;
+                if (!(ok = take(a0))) break;
+                const uint32_t b0 = a0 + 2 * KF::PL;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) {
+                    const uint32_t off = k * 32;
+                    const uint64_t ah = sdesc(a0 + off), al = sdesc(a0 + KF::PL + off);
+                    const uint64_t bh = sdesc(b0 + off), bl = sdesc(b0 + KF::PP + off);
+                    const uint32_t acc = (k1 > 0 || k > 0) ? 1u : 0u;
+                    umma(xa, ah, bh, idesc, acc);
+                    umma(xa, ah, bl, idesc, 1u);
+                    umma(xa, al, bh, idesc, 1u);
+                }
+                release();
+            }
+            if (!ok) break;
+            umma_commit(smem_u32(&xacc_full[b]));
+            if (hp && !(ok = issue_p2(prev, gc - 1))) break;
+            prev = cur;
+            hp = true;
+            ++gc;
+        }
+        if (ok && hp) issue_p2(prev, gc - 1);
+        // every MMA of this thread has completed before TMEM may be freed
+        umma_commit(smem_u32(&mma_done));
+        mbar_wait(smem_u32(&mma_done), 0u);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: split each X chunk, drain Y per item
+        const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+        const int part = (warp - 2) >> 2;   // column part: 16 X columns, 64 Y columns
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = uint32_t(quad * 32) << 16;
+        auto wait_all = [&](uint64_t& bar, uint32_t parity, int code) -> bool {
+            if (__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar), parity))) return true;
+            if (lane == 0) atomicExch(err, code);
+            vstore(abort_s, 1);
+            return false;
+        };
+        auto arrive = [&](uint64_t& bar) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar));
+        };
+        FIter it;
+        FChunk ch;
+        int gc = 0;
+        while (!vload(abort_s) && fnext(works, nworks, segs, it, ch)) {
+            // X chunk: TMEM FP32 -> BF16 (hi, lo) pairs back into TMEM
+            const int b = gc & 1;
+            if (!wait_all(xacc_full[b], uint32_t((gc >> 1) & 1), 16)) break;
+            tc_fence_after();
+            const bool act = part * 16 < ch.n1;  // warp-uniform: columns P1 wrote
+            uint32_t ph[8], pl[8];
+            if (act) {
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_off + KF::XACC + b * KF::XSTEP + part * 16, r);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    // x - bf16(x) is exact in FP32, so the split needs no FP64
+                    const float x0 = __uint_as_float(r[2 * i]), x1 = __uint_as_float(r[2 * i + 1]);
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                    ph[i] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+                    pl[i] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+                }
+            }
+            arrive(xacc_free[b]);
+            if (gc >= 2 && !wait_all(xbf_free[b], uint32_t(((gc >> 1) - 1) & 1), 17)) break;
+            tc_fence_after();
+            if (act) {
+                tmem_st8(tmem + lane_off + KF::XHI + b * KF::XSTEP + part * 8, ph);
+                tmem_st8(tmem + lane_off + KF::XLO + b * KF::XSTEP + part * 8, pl);
+                tmem_st_wait();
+            }
+            arrive(xbf_full[b]);
+            ++gc;
+            if (!ch.last) continue;
+            // end of the item: Y -> FP32 partial tile
+            if (!wait_all(y_full, uint32_t(ch.item & 1), 18)) break;
+            tc_fence_after();
+            float y[64];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (part * 64 + c * 16 < ch.n2) {  // warp-uniform: columns the MMAs wrote
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_off + KF::Y + part * 64 + c * 16, r);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) y[c * 16 + i] = __uint_as_float(r[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) y[c * 16 + i] = 0.f;
+                }
+            }
+            arrive(y_empty);
+            // column-pair-major partial tile (256 contiguous bytes per warp store)
+            float2* out = reinterpret_cast<float2*>(works[ch.wi].out);
+#pragma unroll
+            for (int i = 0; i < 64; i += 2) out[(long long)(part * 32 + i / 2) * BM + row] = make_float2(y[i], y[i + 1]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(KF::TMEM_COLS) : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ helpers
 // Operand splitting.  Element (r, c) of the source is src[r * rs + c * cs];
 // columns from cols to ldd - 1 are zero padding; plane k of the output
@@ -772,6 +1144,34 @@ CUtensorMap make_map(const void* base, int K, long long rows, int layers, int ld
     strides[rank - 1] = cuuint64_t(std::max<long long>(plane_pitch, 8)) * 2;
     box[rank++] = 1;
     CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GBD_REQUIRE(r == CUDA_SUCCESS, GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+// BF16 K-major operand with up to two outer dimensions of any element
+// strides (multiples of 8), then the slice planes; box BK x box1 x box2.
+CUtensorMap make_map_n(const void* base, int K, int nd, const long long* dims, const long long* strides, const int* box,
+                       int planes, long long plane_pitch) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    GBD_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0 && plane_pitch % 8 == 0 && nd >= 1 && nd <= 2,
+                GBD_ERR_STATE, "TMA operand misaligned");
+    cuuint64_t gd[4], gs[3];
+    cuuint32_t bx[4], es[4] = {1, 1, 1, 1};
+    gd[0] = cuuint64_t(std::max(K, 1));
+    bx[0] = cuuint32_t(BK);
+    for (int i = 0; i < nd; ++i) {
+        GBD_REQUIRE(strides[i] % 8 == 0 && box[i] >= 1 && box[i] <= 256, GBD_ERR_STATE, "TMA operand misaligned");
+        gd[1 + i] = cuuint64_t(std::max<long long>(dims[i], 1));
+        gs[i] = cuuint64_t(strides[i]) * 2;
+        bx[1 + i] = cuuint32_t(box[i]);
+    }
+    gd[1 + nd] = cuuint64_t(std::max(planes, 1));
+    gs[nd] = cuuint64_t(std::max<long long>(plane_pitch, 8)) * 2;
+    bx[1 + nd] = 1;
+    CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(nd + 2), const_cast<void*>(base), gd, gs, bx, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     GBD_REQUIRE(r == CUDA_SUCCESS, GBD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -1006,40 +1406,35 @@ template <int MODE> void build_ops(Ctx& C, int side) {
     (side == 0 ? P.ops_l : P.ops_r) = true;
 }
 
-// Phase-2 work list of one product form: per output sector tile, the K
-// chunks of all its (class, input sector) segments split into near-equal
-// ranges (split-K), one FP64 reduction per tile.
-template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
-    constexpr int TBN = ModeCfg<MODE>::BN2;
-    constexpr bool pairs = KT<MODE, 2>::PAIRS;
+// Split-K work list over the output sector tiles: per tile (BM x TBN) the K
+// chunks of all its segments (Seg: KSeg of the phase-2 kernel or FSeg of the
+// fused kernel) split into near-equal ranges, one FP64 reduction per tile;
+// max_chunks > 0 caps the chunks of one item.
+template <class Seg>
+void build_items(Ctx& C, const std::vector<Seg>& segs, const std::vector<std::vector<int>>& seg_of_out, int TBN,
+                 bool pairs, int promote, int max_chunks, const TuneParams& tp, std::vector<Work>& w2,
+                 std::vector<Reduce>& red, std::vector<Seg>& s2o, long long& npart) {
     Heff& H = C.H;
-    TcHeff& T = H.tc;
-    TcPlan& P = T.pl[MODE];
-    cudaStream_t st = C.cs;
-    const std::vector<KSeg>& s2 = P.s2_host;
-    const std::vector<std::vector<int>>& seg_of_out = P.seg_of_out;
-    std::vector<Work> w2;
-    std::vector<Reduce> red;
     long long total_chunks = 0;
     for (size_t q = 0; q < H.sq.size(); ++q) {
         long long c = 0;
-        for (int si : seg_of_out[q]) c += s2[si].nchunk;
+        for (int si : seg_of_out[q]) c += segs[si].nchunk;
         int tiles = ((H.bL.dim[H.sL[q]] + BM - 1) / BM) * ((H.bR.dim[H.sR[q]] + TBN - 1) / TBN);
         total_chunks += c * tiles;
     }
-    const long long target = std::max<long long>(16, total_chunks / ((long long)tp.split_per_sm * T.n_sm) + 1);
-    std::vector<KSeg> s2o;  // segments re-laid per output sector (contiguous)
-    long long npart = 0;
+    long long target = std::max<long long>(16, total_chunks / ((long long)tp.split_per_sm * H.tc.n_sm) + 1);
+    if (max_chunks > 0) target = std::min<long long>(target, max_chunks);
+    npart = 0;
     for (size_t q = 0; q < H.sq.size(); ++q) {
         int seg0 = int(s2o.size());
         int nchunk = 0;
-        for (int si : seg_of_out[q]) { s2o.push_back(s2[si]); nchunk += s2[si].nchunk; }
+        for (int si : seg_of_out[q]) { s2o.push_back(segs[si]); nchunk += segs[si].nchunk; }
         int nseg = int(s2o.size()) - seg0;
         const int mL = H.bL.dim[H.sL[q]], mR = H.bR.dim[H.sR[q]];
         // one reduction (and a run of partials) per output tile; order 0 lists
         // the items K range by K range, so the tiles of one sector that read
-        // the same K chunks of X and O^xR run side by side and share them in
-        // L2; order 1 lists them tile by tile
+        // the same K chunks run side by side and share them in L2; order 1
+        // lists them tile by tile
         const int nrange = int((nchunk + target - 1) / target);
         const size_t r0 = red.size();
         for (int m0 = 0; m0 < mL; m0 += BM)
@@ -1072,10 +1467,10 @@ template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
             w.c0 = c0;
             w.c1 = int(std::min<long long>(nchunk, c0 + target));
             w.out_kind = 0;
-            w.promote = MODE == 0 ? 8 : 1;
+            w.promote = promote;
             w.ldo = TBN;
             w.colcap = TBN;
-            w.out = reinterpret_cast<void*>((long long)r.p0 + k);  // patched to a pointer below
+            w.out = reinterpret_cast<void*>((long long)r.p0 + k);  // patched to a pointer by the caller
             w2.push_back(w);
         };
         if (tp.order == 0) {
@@ -1086,13 +1481,58 @@ template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
                 for (int k = 0; k < nrange; ++k) item(ti, k);
         }
     }
+}
+
+// tensor-core GFLOP the fused work list issues per product (P1 and P2 of
+// every chunk at their MMA widths, three split products each)
+void issued_fused(const std::vector<Work>& ws, const std::vector<FSeg>& segs, double& p1, double& p2) {
+    p1 = p2 = 0.0;
+    for (const auto& w : ws) {
+        const int v2 = w.N - w.n0;
+        const int n2 = v2 >= KF::BN ? KF::BN : ((v2 + 15) & ~15);
+        int s = w.seg0, c = w.c0;
+        while (s < w.seg0 + w.nseg && c >= segs[s].nchunk) { c -= segs[s].nchunk; ++s; }
+        for (int k = w.c0; k < w.c1 && s < w.seg0 + w.nseg; ++k) {
+            const FSeg& g = segs[s];
+            const int j0 = (c % g.ncol) * FN, v1 = g.mRi - j0;
+            const int n1 = v1 >= FN ? FN : ((v1 + 15) & ~15);
+            p1 += double(BM) * n1 * (g.nk1 * BK) * 2.0 * 3.0;
+            p2 += double(BM) * n2 * n1 * 2.0 * 3.0;
+            if (++c >= g.nchunk) { c = 0; ++s; }
+        }
+    }
+    p1 *= 1e-9;
+    p2 *= 1e-9;
+}
+
+// Phase-2 work list of one product form (BF16x3 fused: the fused kernel's).
+template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
+    constexpr int TBN = ModeCfg<MODE>::BN2;
+    constexpr bool pairs = KT<MODE, 2>::PAIRS;
+    TcPlan& P = C.H.tc.pl[MODE];
+    cudaStream_t st = C.cs;
+    const bool fused = MODE == 0 && P.fused;
+    const int bn = fused ? KF::BN : TBN;
+    std::vector<Work> w2;
+    std::vector<Reduce> red;
+    long long npart = 0;
+    if (fused) {
+        std::vector<FSeg> s2o;
+        // an item accumulates at most kFusedChunks chunks (K = 2048) in TMEM
+        build_items(C, P.f_host, P.seg_of_out, bn, false, 0, kFusedChunks, tp, w2, red, s2o, npart);
+        issued_fused(w2, s2o, P.issued_p1, P.issued_p2);
+        upload_vec(P.s2, s2o, st);
+    } else {
+        std::vector<KSeg> s2o;
+        build_items(C, P.s2_host, P.seg_of_out, bn, pairs, MODE == 0 ? 8 : 1, 0, tp, w2, red, s2o, npart);
+        P.issued_p2 = issued_gflop<MODE, 2>(w2);
+        upload_vec(P.s2, s2o, st);
+    }
     // partial tiles: float2 (hi, lo) per element, or one float per element
-    P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * TBN * sizeof(float2), st);
+    P.partial.ensure_cached(size_t(std::max<long long>(npart, 1)) * BM * bn * sizeof(float2), st);
     for (auto& w : w2)
-        w.out = reinterpret_cast<float*>(P.partial.p) + reinterpret_cast<long long>(w.out) * BM * TBN * (pairs ? 2 : 1);
-    P.issued_p2 = issued_gflop<MODE, 2>(w2);
+        w.out = reinterpret_cast<float*>(P.partial.p) + reinterpret_cast<long long>(w.out) * BM * bn * (pairs ? 2 : 1);
     upload_vec(P.w2, w2, st);
-    upload_vec(P.s2, s2o, st);
     upload_vec(P.red, red, st);
     P.n_w2 = int(w2.size());
     P.n_red = int(red.size());
@@ -1147,10 +1587,13 @@ template <int MODE> void build_plan(Ctx& C) {
         return H.bL.dim[H.sL[a.si]] > H.bL.dim[H.sL[b.si]];
     });
     P.nx = std::max(nx, 8LL);
+    // the fused BF16x3 kernel keeps X on the SM: no phase-1 buffer
+    P.fused = MODE == 0 && C.cfg.bf16x3_fused != 0 && !T.two_phase;
+    P.f_host.clear();
     // one phase-1 buffer serves both forms (they never run at the same time):
     // sized for the four slice planes of the sliced form
-    T.x.ensure_cached(size_t(P.nx) * ModeCfg<1>::NS * 2, st);
-    __nv_bfloat16* const xbase = T.x.as<__nv_bfloat16>();
+    if (!P.fused) T.x.ensure_cached(size_t(P.nx) * ModeCfg<1>::NS * 2, st);
+    __nv_bfloat16* const xbase = P.fused ? nullptr : T.x.as<__nv_bfloat16>();
     // ---- tensor maps: one per operand, the NS slice planes as outer dimension
     std::vector<CUtensorMap> maps;
     auto add_maps = [&](const __nv_bfloat16* base, long long plane, int K, long long rows, int layers, int ld,
@@ -1162,7 +1605,8 @@ template <int MODE> void build_plan(Ctx& C) {
     std::vector<int> psi_map(H.sq.size());
     for (size_t s = 0; s < H.sq.size(); ++s) {
         const auto& ps = T.psec[s];
-        psi_map[s] = add_maps(P.psi.as<__nv_bfloat16>() + ps.dst, P.np, ps.mL, ps.mR, 0, ps.ldp, 0, TBN);
+        // box rows: the phase-1 tile columns, or one X chunk of the fused kernel
+        psi_map[s] = add_maps(P.psi.as<__nv_bfloat16>() + ps.dst, P.np, ps.mL, ps.mR, 0, ps.ldp, 0, P.fused ? FN : TBN);
     }
     std::vector<KSeg> s1, s2;
     std::vector<Work> w1;
@@ -1172,8 +1616,32 @@ template <int MODE> void build_plan(Ctx& C) {
         const int Tn = int(cl.states.size());
         const int mLo = H.bL.dim[H.sL[p.so]], mLi = H.bL.dim[H.sL[p.si]];
         const int mRo = H.bR.dim[H.sR[p.so]], mRi = H.bR.dim[H.sR[p.si]];
-        // phase 1: X (Tn*mLo x mRi) = OL_stacked (Tn*mLo x mLi) psi (mLi x mRi), psi^T K-major
         const long long ol = offL[p.c][p.bl];
+        const long long orr = offR[p.c][p.br];
+        if (MODE == 0 && P.fused) {
+            // O^Lx block (mLi, mLo, Tn) and O^xR block (mRi, Tn, mRo), both K-major
+            const long long dl[2] = {mLo, Tn}, sl[2] = {pad8(mLi), (long long)mLo * pad8(mLi)};
+            const long long dr[2] = {Tn, mRo}, sr[2] = {pad8(mRi), (long long)Tn * pad8(mRi)};
+            const int bl[2] = {BM, 1}, br[2] = {1, KF::BN};
+            const int mL_ = int(maps.size());
+            maps.push_back(make_map_n(P.ol.as<__nv_bfloat16>() + ol, mLi, 2, dl, sl, bl, NS, P.nL));
+            const int mR_ = int(maps.size());
+            maps.push_back(make_map_n(P.orr.as<__nv_bfloat16>() + orr, mRi, 2, dr, sr, br, NS, P.nR));
+            FSeg f{};
+            f.mapL = mL_;
+            f.mapP = psi_map[p.si];
+            f.mapR = mR_;
+            f.mLi = mLi;
+            f.mRi = mRi;
+            f.T = Tn;
+            f.nk1 = (mLi + BK - 1) / BK;
+            f.ncol = (mRi + FN - 1) / FN;
+            f.nchunk = Tn * f.ncol;
+            seg_of_out[p.so].push_back(int(P.f_host.size()));
+            P.f_host.push_back(f);
+            continue;
+        }
+        // phase 1: X (Tn*mLo x mRi) = OL_stacked (Tn*mLo x mLi) psi (mLi x mRi), psi^T K-major
         int mA = add_maps(P.ol.as<__nv_bfloat16>() + ol, P.nL, mLi, (long long)Tn * mLo, 0, pad8(mLi), 0, BM);
         int sidx = int(s1.size());
         s1.push_back({mA, psi_map[p.si], 0, 0, mLi, 1, 2, (mLi + BK - 1) / BK});
@@ -1203,7 +1671,6 @@ template <int MODE> void build_plan(Ctx& C) {
                 w.out = xbase + p.x;
                 w1.push_back(w);
             }
-        const long long orr = offR[p.c][p.br];
         seg_of_out[p.so].push_back(int(s2.size()));
         if (MODE == 0) {
             // phase 2 operands with layers side by side: X (mLo x Tn*ldk),
@@ -1225,7 +1692,7 @@ template <int MODE> void build_plan(Ctx& C) {
     P.seg_of_out = seg_of_out;
     // tensor-core work issued per product (whole 128-row tiles at the MMA
     // width, every slice product): the gap to the useful flops is padding
-    P.issued_p1 = issued_gflop<MODE, 1>(w1);
+    if (!P.fused) P.issued_p1 = issued_gflop<MODE, 1>(w1);
     if (MODE == 0) tune_begin(C);
     build_p2<MODE>(C, MODE == 0 ? tune_params(H.tc.tune) : TuneParams{});
     // persistent CTAs take items round-robin: w1 is longest first by
@@ -1240,6 +1707,8 @@ template <int MODE> void build_plan(Ctx& C) {
                                         KT<MODE, 1>::SMEM_BYTES));
     GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         KT<MODE, 2>::SMEM_BYTES));
+    if (P.fused)
+        GBD_CHECK_CUDA(cudaFuncSetAttribute(tc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KF::SMEM_BYTES));
     GBD_CHECK_CUDA(cudaStreamSynchronize(st));
     P.built = true;
     C.timers[Ctx::T_PREP_SPLIT] += t1 - t0;
@@ -1390,7 +1859,11 @@ template <int MODE> void run_plan(Ctx& C) {
         count_launch();
     }
     if (P.n_red > 0) {
-        if (P.n_w2 > 0) {
+        if (P.n_w2 > 0 && MODE == 0 && P.fused) {
+            tc_fused_kernel<<<std::min(P.n_w2, T.n_sm), THREADS, KF::SMEM_BYTES, st>>>(
+                P.w2.as<Work>(), P.n_w2, P.s2.as<FSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
+            count_launch();
+        } else if (P.n_w2 > 0) {
             tc_gemm_kernel<MODE, 2><<<std::min(P.n_w2, T.n_sm), THREADS, KT<MODE, 2>::SMEM_BYTES, st>>>(
                 P.w2.as<Work>(), P.n_w2, P.s2.as<KSeg>(), P.maps.as<CUtensorMap>(), T.err.as<int>());
             count_launch();

@@ -78,6 +78,23 @@ struct Work {
     void* out;
 };
 
+// One segment of the fused BF16x3 product: a (class, left block, right
+// block) pair feeding one output sector.  Its chunks run over the layers
+// t < T and over column blocks of FN columns of the input right sector; a
+// chunk computes X_t(rows of the tile, FN columns) = O^Lx_t psi on the
+// tensor cores (K = mLi) and multiplies it at once into the output tile
+// (K = FN), so X never leaves the SM.
+constexpr int FN = 64;
+struct FSeg {
+    int mapL;          // O^Lx block: dims (mLi, mLo, T), layer-stacked rows
+    int mapP;          // psi^T of the input sector: dims (mLi, mRi)
+    int mapR;          // O^xR block: dims (mRi, T, mRo), layers side by side along each row
+    int mLi, mRi, T;
+    int nk1;           // ceil(mLi / BK): K chunks of one X chunk
+    int ncol;          // ceil(mRi / FN): column blocks per layer
+    int nchunk;        // T * ncol
+};
+
 // Sum of split-K partial tiles into one FP64 output tile.
 struct Reduce {
     double* out;
@@ -120,7 +137,9 @@ struct TcPlan {
     int n_w1 = 0, n_w2 = 0, n_red = 0, n_psi = 0;
     double bytes_ops = 0.0;                     // operator slice bytes
     double issued_p1 = 0.0, issued_p2 = 0.0;    // tensor-core GFLOP issued per product
+    bool fused = false;                         // BF16x3: one fused kernel (s2 holds FSeg), no phase 1
     std::vector<tc::KSeg> s2_host;              // phase-2 segments per pair (host, for re-planning)
+    std::vector<tc::FSeg> f_host;               // fused segments per pair (host, for re-planning)
     std::vector<std::vector<int>> seg_of_out;   // phase-2 segments of each output sector
 };
 
@@ -129,6 +148,7 @@ struct TcHeff {
     DevBuf x;                               // phase-1 output X, shared by both forms
     TcTune tune;                            // BF16x3 phase-2 autotuner
     bool low_mem = false;                   // FP64 enlarged arenas released after the planes were built
+    bool two_phase = false;                 // the next BF16x3 plan: two kernels whatever the config says
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
     std::vector<PsiSec> psec;

@@ -78,8 +78,9 @@ def test_davidson_product_limit_is_a_warning():
 
 
 def test_mixed_davidson_reports_its_precision_floor():
-    # a tolerance below what BF16x3 products can resolve: after three anchors
-    # the mixed Davidson stops and says so (the energy is the last anchor's)
+    # a tolerance below what the anchor products can resolve: once an anchor
+    # no longer halves the exact residual the mixed Davidson stops and says so
+    # (the result is its best anchored pair)
     L, N, D, b = 8, 8, 24, 3
     h, eri = inputs.make_integrals(L, 45)
     sites, dims = inputs.make_mps(L, N, 0, D, 46, n_left=b)
