@@ -79,13 +79,15 @@ enum {
  * 2^-30 relative to the row maxima).  GBD_SLICED_BF16 is a product form for
  * gbd_apply_heff and for Davidson anchors (mixed_polish = 2), not a
  * context precision. */
-enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2, GBD_FP64_PER_BLOCK = 3, GBD_BF16X3_TWO_PHASE = 4 };
+enum { GBD_FP64 = 0, GBD_MIXED_BF16X3 = 1, GBD_SLICED_BF16 = 2, GBD_FP64_PER_BLOCK = 3, GBD_BF16X3_TWO_PHASE = 4,
+       GBD_BF16X3_FUSED = 5 };
 /* GBD_FP64_PER_BLOCK: the FP64 product with one kernel launch per sector
  * block GEMM task instead of one grouped launch per phase (same kernel, same
  * tiles, bitwise the same result); a comparison form for gbd_apply_heff.
- * GBD_BF16X3_TWO_PHASE: the BF16x3 product in two kernels with X stored in
- * HBM between them, whatever gbd_config.bf16x3_fused says (same split
- * products, another summation order); a comparison form for gbd_apply_heff. */
+ * GBD_BF16X3_TWO_PHASE / GBD_BF16X3_FUSED: the BF16x3 product in two
+ * kernels with X stored in HBM between them / in the fused kernel, whatever
+ * gbd_config.bf16x3_fused says (same split products, another summation
+ * order); comparison forms for gbd_apply_heff. */
 
 typedef struct gbd_ctx gbd_ctx;
 
@@ -153,12 +155,14 @@ typedef struct {
                            buffer would not fit beside them; 1: always;
                            -1: never.  A later GBD_FP64 product at the same
                            position enlarges the operators again.          */
-    int bf16x3_fused;   /* BF16x3 products: 1 (default) one fused kernel per
-                           product (each chunk of X = O^Lx psi is formed in
-                           tensor memory, split into BF16 hi / lo there and
-                           multiplied at once into the output tile, so X
-                           never reaches HBM); 0: two kernels with X stored
-                           in HBM between them                             */
+    int bf16x3_fused;   /* BF16x3 products: 0 (default) two kernels with X
+                           stored in HBM between them; 1: one fused kernel
+                           per product (each chunk of X = O^Lx psi is formed
+                           in tensor memory, split into BF16 hi / lo there
+                           and multiplied at once into the output tile, so X
+                           never reaches HBM; half the DRAM traffic, but
+                           slower on GB300: its chunk-by-chunk split is a
+                           latency chain and its first MMAs are 64 wide)  */
 } gbd_config;
 
 /* Host-side fault injection (gbd_config.fault_inject).  Each failure is made
@@ -308,7 +312,7 @@ int gbd_build_tables(gbd_ctx* ctx, int b, gbd_sector_info* out, int cap, int* n,
  * sector-major layout above, FP64.  on_device = 1: both pointers are device
  * pointers; 0: host pointers (copied in and out).  precision selects the
  * product form (GBD_FP64, GBD_MIXED_BF16X3, GBD_SLICED_BF16,
- * GBD_FP64_PER_BLOCK or GBD_BF16X3_TWO_PHASE).  psi_out may not alias psi_in. */
+ * GBD_FP64_PER_BLOCK, GBD_BF16X3_TWO_PHASE or GBD_BF16X3_FUSED).  psi_out may not alias psi_in. */
 int gbd_apply_heff(gbd_ctx* ctx, int b, const double* psi_in, double* psi_out, int on_device, int precision);
 
 /* Diagonal of H_eff at b (for preconditioning / checks), same layout. */
@@ -486,7 +490,7 @@ int gbd_tune_reset(void);
  * (env_recompute) and the number of environments it rebuilt, then the GB
  * written to and read back from the spill file and the host time (ms) spent
  * waiting for spill jobs (host_store_bytes), then the device time (ms) and
- * number of GBD_BF16X3_TWO_PHASE products.
+ * number of GBD_BF16X3_TWO_PHASE products, then of GBD_BF16X3_FUSED products.
  * *n gets the count; out may be NULL. */
 int gbd_timers(gbd_ctx* ctx, double* out, int cap, int* n);
 

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libgbdmrg.so")
 HEADER = os.path.join(HERE, "..", "include", "gbdmrg.h")
 
-FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK, BF16X3_TWO_PHASE = 0, 1, 2, 3, 4
+FP64, MIXED_BF16X3, SLICED_BF16, FP64_PER_BLOCK, BF16X3_TWO_PHASE, BF16X3_FUSED = 0, 1, 2, 3, 4, 5
 FAULT_PINNED_ALLOC, FAULT_IO_NEVER_READY, FAULT_CORRUPT_HOST_COPY = 1, 2, 4
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_DEVICE_OOM", -3: "GBD_ERR_HOST_OOM", -4: "GBD_ERR_CUDA",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_CORRUPT", -7: "GBD_ERR_STATE"}
@@ -246,7 +246,7 @@ class Context:
     def __init__(self, L, N, tsz, D=256, precision=FP64, offload=False, device=0, dav_tol=1e-8,
                  dav_max_sub=24, dav_keep=4, dav_max_matvec=200, switch_cut=0, io_timeout_ms=120000, seed=12345,
                  mixed_fp64_blocks=False, mixed_polish=2, fault_inject=0, low_memory=0, autotune=True,
-                 env_recompute=0, host_store_bytes=0, bf16x3_fused=True):
+                 env_recompute=0, host_store_bytes=0, bf16x3_fused=False):
         cfg = Config()
         _check(lib().gbd_config_default(C.byref(cfg)))
         cfg.L, cfg.N, cfg.tsz, cfg.D, cfg.precision = L, N, tsz, D, precision
@@ -431,7 +431,8 @@ class Context:
               "step_next", "step_io", "enlarge_host_links", "enlarge_host_subs", "enlarge_host_items",
               "products_bf16x3_gbytes", "products_bf16x3_x_gbytes", "products_fp64_per_block_ms",
               "products_fp64_per_block_n", "recompute_ms", "recompute_n", "spill_gbytes", "restore_gbytes",
-              "spill_wait_ms", "products_bf16x3_two_phase_ms", "products_bf16x3_two_phase_n"]
+              "spill_wait_ms", "products_bf16x3_two_phase_ms", "products_bf16x3_two_phase_n",
+              "products_bf16x3_fused_ms", "products_bf16x3_fused_n"]
 
     def timers(self):
         out = np.zeros(64)

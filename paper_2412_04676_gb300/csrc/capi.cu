@@ -68,7 +68,7 @@ int gbd_config_default(gbd_config* cfg) {
     cfg->autotune = 1;
     cfg->env_recompute = 0;
     cfg->host_store_bytes = 0;
-    cfg->bf16x3_fused = 1;
+    cfg->bf16x3_fused = 0;
     return GBD_OK;
 }
 
@@ -219,7 +219,8 @@ int gbd_apply_heff(gbd_ctx* c, int b, const double* psi_in, double* psi_out, int
         Ctx& C = ctx(c);
         GBD_REQUIRE(psi_in && psi_out && psi_in != psi_out, GBD_ERR_ARG, "bad vectors");
         GBD_REQUIRE(precision == GBD_FP64 || precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 ||
-                        precision == GBD_FP64_PER_BLOCK || precision == GBD_BF16X3_TWO_PHASE, GBD_ERR_ARG,
+                        precision == GBD_FP64_PER_BLOCK || precision == GBD_BF16X3_TWO_PHASE ||
+                        precision == GBD_BF16X3_FUSED, GBD_ERR_ARG,
                     "bad precision");
         ensure_heff(C, b);
         Heff& H = C.H;

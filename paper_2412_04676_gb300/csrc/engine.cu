@@ -1057,14 +1057,14 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     Heff& H = C.H;
     GBD_CHECK_CUDA(cudaMemcpyAsync(H.xin.p, in, size_t(H.dim) * sizeof(double), cudaMemcpyDeviceToDevice, C.cs));
     GBD_CHECK_CUDA(cudaEventRecord(C.ev0, C.cs));
-    const bool two = precision == GBD_BF16X3_TWO_PHASE;
-    const bool tensor = precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 || two;
+    const bool two = precision == GBD_BF16X3_TWO_PHASE, fz = precision == GBD_BF16X3_FUSED;
+    const bool tensor = precision == GBD_MIXED_BF16X3 || precision == GBD_SLICED_BF16 || two || fz;
     const int mode = precision == GBD_SLICED_BF16 ? 1 : 0;
     if (tensor) {
         // the BF16x3 plan is fused or two-phase: a request for the other form re-plans it
-        if (mode == 0 && H.tc_ready && H.tc.pl[0].built && H.tc.pl[0].fused == (two || !C.cfg.bf16x3_fused))
-            H.tc.pl[0].built = false;
-        if (mode == 0) H.tc.two_phase = two;
+        const bool want_fused = fz || (precision == GBD_MIXED_BF16X3 && C.cfg.bf16x3_fused);
+        if (mode == 0 && H.tc_ready && H.tc.pl[0].built && H.tc.pl[0].fused != want_fused) H.tc.pl[0].built = false;
+        if (mode == 0) H.tc.want_fused = want_fused;
         if (!H.tc_ready || !H.tc.pl[mode].built) {
             const double tt0 = wall_ms();
             tc_prepare(C, mode);
@@ -1102,6 +1102,9 @@ void apply_heff_dev(Ctx& C, const double* in, double* out, int precision) {
     } else if (two) {
         C.timers[Ctx::T_PROD_MS_TP] += ms;
         C.timers[Ctx::T_PROD_N_TP] += 1.0;
+    } else if (fz) {
+        C.timers[Ctx::T_PROD_MS_FZ] += ms;
+        C.timers[Ctx::T_PROD_N_FZ] += 1.0;
     } else {
         C.timers[Ctx::T_PROD_MS0 + precision] += ms;
         C.timers[Ctx::T_PROD_N0 + precision] += 1.0;
@@ -1334,7 +1337,11 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
                 // < 10% gain in 6 iterations, near the mixed floor (~1e-5 |theta|)
                 stalled = recent > 0.9 * before && rn <= 1e-4 * std::max(1.0, std::fabs(theta));
             }
-            anchor = rn <= tol || stalled || nmv >= C.cfg.dav_max_matvec || (exact0 && k >= kmax);
+            // before the first anchor the mixed residual cannot go much below
+            // the products' rounding (~3e-6 |theta| measured): anchor at
+            // 1e-5 |theta| rather than iterate at the floor
+            const double first = anchors == 0 ? 1e-5 * std::fabs(theta) : 0.0;
+            anchor = rn <= std::max(tol, first) || stalled || nmv >= C.cfg.dav_max_matvec || (exact0 && k >= kmax);
             if (k == 1 && exact_start && anchors == 0 && iters == 1) {
                 // the residual of the start vector is already exact
                 if (rn <= C.cfg.dav_tol) break;

@@ -137,7 +137,7 @@ struct Ctx {
            // device time of the phases of gbd_step on the compute stream (host gaps included)
            T_PH_RESIDENT, T_PH_ENLARGE, T_PH_DAVIDSON, T_PH_RHO_EIG, T_PH_RENORM, T_PH_NEXT, T_PH_IO,
            T_ENL_H_LINKS, T_ENL_H_SUBS, T_ENL_H_ITEMS, T_PROD_GB1, T_PROD_XGB1, T_PROD_MS_PB, T_PROD_N_PB, T_RECOMP_MS, T_RECOMP_N,
-           T_SPILL_GB, T_RESTORE_GB, T_SPILL_WAIT_MS, T_PROD_MS_TP, T_PROD_N_TP, T_COUNT };
+           T_SPILL_GB, T_RESTORE_GB, T_SPILL_WAIT_MS, T_PROD_MS_TP, T_PROD_N_TP, T_PROD_MS_FZ, T_PROD_N_FZ, T_COUNT };
     std::vector<std::pair<int, cudaEvent_t>> marks;  // phase boundaries of the running step
     std::vector<cudaEvent_t> mark_pool;
     double timers[T_COUNT] = {0};

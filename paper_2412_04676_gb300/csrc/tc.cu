@@ -17,8 +17,8 @@
 // fill of TMA boxes handles ragged sector edges.  Every spin-wait is
 // bounded: on expiry the CTA records an error code in a device word, stops
 // issuing, waits (bounded) for its copies and frees TMEM.
-// The BF16x3 product also runs as one fused kernel (tc_fused_kernel, the
-// default): each chunk of X is formed in TMEM, split there and multiplied
+// The BF16x3 product also runs as one fused kernel (tc_fused_kernel, an
+// option): each chunk of X is formed in TMEM, split there and multiplied
 // into the output tile at once, so X never reaches HBM.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -289,7 +289,21 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             // MMA width: the tile's valid columns rounded up to 16 (M = 128 needs N % 16 == 0)
             const uint32_t idesc = (K_::IDESC & ~(0x3Fu << 17)) | (uint32_t(tile_n(w) >> 3) << 17);
             int inbuf = 0;
+            // the chunk's position, as the producer walks it: K steps of 16
+            // wholly past the segment's K read zero fill and are skipped
+            int ks, kt, kj0;
+            locate(segs, w.seg0, w.nseg, w.c0, ks, kt, kj0);
             for (int i = 0; i < n; ++i, ++g) {
+                int kst = BK / 16;
+                if (ks < w.seg0 + w.nseg) {
+                    const int kk = segs[ks].K;
+                    kst = (max(1, min(BK, kk - kj0)) + 15) / 16;  // at least one step: the buffer's first MMA clears it
+                    kj0 += BK;
+                    if (kj0 >= kk) {
+                        kj0 = 0;
+                        if (++kt >= segs[ks].T) { kt = 0; ++ks; }
+                    }
+                }
                 const int st = int(g % K_::ST);
                 if (!mbar_wait(smem_u32(&full_bar[st]), uint32_t((g / K_::ST) & 1))) {
                     atomicExch(err, 2);
@@ -312,6 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const uint32_t d = tmem + uint32_t(buf * K_::BUFCOLS);
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k) {
+                    if (k >= kst) break;
                     const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
                     const uint32_t acc = (inbuf > 0 || k > 0) ? 1u : 0u;
                     if constexpr (MODE == 0) {
@@ -849,8 +864,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fused_kernel(const Work* __rest
                 uint32_t a0;
                 if (!(ok = take(a0))) break;
                 const uint32_t b0 = a0 + 2 * KF::PL;
+                const int kst = (max(1, min(BK, sg.mLi - k1 * BK)) + 15) / 16;  // K steps past mLi read zero fill
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k) {
+                    if (k >= kst) break;
                     const uint32_t off = k * 32;
                     const uint64_t ah = sdesc(a0 + off), al = sdesc(a0 + KF::PL + off);
                     const uint64_t bh = sdesc(b0 + off), bl = sdesc(b0 + KF::PP + off);
@@ -1291,13 +1308,23 @@ void build_block_terms(Ctx& C, TcPlan& P, const std::vector<std::vector<long lon
 
 // tensor-core GFLOP a work list issues (whole 128-row tiles at the MMA width,
 // every split or slice product): the gap to the useful flops is padding
-template <int MODE, int PH> double issued_gflop(const std::vector<Work>& ws) {
+template <int MODE, int PH> double issued_gflop(const std::vector<Work>& ws, const std::vector<KSeg>& segs) {
     constexpr int TBN = PH == 2 ? ModeCfg<MODE>::BN2 : ModeCfg<MODE>::BN;
     double f = 0.0;
     for (const auto& w : ws) {
         const int v = w.N - w.n0;
         const int nn = v >= TBN ? TBN : ((v + 15) & ~15);  // the kernel's MMA width
-        f += double(w.c1 - w.c0) * BM * nn * BK * 2.0 * (MODE == 0 ? 3.0 : 10.0);
+        // K steps of 16 the kernel issues over the item's chunks
+        long long ksteps = 0;
+        int s = w.seg0, c = w.c0;
+        while (s < w.seg0 + w.nseg && c >= segs[s].nchunk) { c -= segs[s].nchunk; ++s; }
+        for (int k = w.c0; k < w.c1 && s < w.seg0 + w.nseg; ++k) {
+            const int kch = (segs[s].K + BK - 1) / BK;
+            const int j0 = (c % kch) * BK;
+            ksteps += (std::max(1, std::min(BK, segs[s].K - j0)) + 15) / 16;
+            if (++c >= segs[s].nchunk) { c = 0; ++s; }
+        }
+        f += double(ksteps) * 16.0 * BM * nn * 2.0 * (MODE == 0 ? 3.0 : 10.0);
     }
     return f * 1e-9;
 }
@@ -1496,7 +1523,7 @@ void issued_fused(const std::vector<Work>& ws, const std::vector<FSeg>& segs, do
             const FSeg& g = segs[s];
             const int j0 = (c % g.ncol) * FN, v1 = g.mRi - j0;
             const int n1 = v1 >= FN ? FN : ((v1 + 15) & ~15);
-            p1 += double(BM) * n1 * (g.nk1 * BK) * 2.0 * 3.0;
+            p1 += double(BM) * n1 * ((g.mLi + 15) / 16 * 16) * 2.0 * 3.0;
             p2 += double(BM) * n2 * n1 * 2.0 * 3.0;
             if (++c >= g.nchunk) { c = 0; ++s; }
         }
@@ -1525,7 +1552,7 @@ template <int MODE> void build_p2(Ctx& C, const TuneParams& tp) {
     } else {
         std::vector<KSeg> s2o;
         build_items(C, P.s2_host, P.seg_of_out, bn, pairs, MODE == 0 ? 8 : 1, 0, tp, w2, red, s2o, npart);
-        P.issued_p2 = issued_gflop<MODE, 2>(w2);
+        P.issued_p2 = issued_gflop<MODE, 2>(w2, s2o);
         upload_vec(P.s2, s2o, st);
     }
     // partial tiles: float2 (hi, lo) per element, or one float per element
@@ -1588,7 +1615,7 @@ template <int MODE> void build_plan(Ctx& C) {
     });
     P.nx = std::max(nx, 8LL);
     // the fused BF16x3 kernel keeps X on the SM: no phase-1 buffer
-    P.fused = MODE == 0 && C.cfg.bf16x3_fused != 0 && !T.two_phase;
+    P.fused = MODE == 0 && T.want_fused;
     P.f_host.clear();
     // one phase-1 buffer serves both forms (they never run at the same time):
     // sized for the four slice planes of the sliced form
@@ -1692,7 +1719,7 @@ template <int MODE> void build_plan(Ctx& C) {
     P.seg_of_out = seg_of_out;
     // tensor-core work issued per product (whole 128-row tiles at the MMA
     // width, every slice product): the gap to the useful flops is padding
-    if (!P.fused) P.issued_p1 = issued_gflop<MODE, 1>(w1);
+    if (!P.fused) P.issued_p1 = issued_gflop<MODE, 1>(w1, s1);
     if (MODE == 0) tune_begin(C);
     build_p2<MODE>(C, MODE == 0 ? tune_params(H.tc.tune) : TuneParams{});
     // persistent CTAs take items round-robin: w1 is longest first by

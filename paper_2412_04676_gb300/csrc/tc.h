@@ -148,7 +148,7 @@ struct TcHeff {
     DevBuf x;                               // phase-1 output X, shared by both forms
     TcTune tune;                            // BF16x3 phase-2 autotuner
     bool low_mem = false;                   // FP64 enlarged arenas released after the planes were built
-    bool two_phase = false;                 // the next BF16x3 plan: two kernels whatever the config says
+    bool want_fused = false;                // the next BF16x3 plan: the fused kernel (set per product)
     // psi split plan: per sector source / destination offsets
     struct PsiSec { long long src, dst; int mL, mR, ldp; };
     std::vector<PsiSec> psec;

@@ -122,6 +122,7 @@ def test_fused_and_two_phase_products_agree(L, N, tsz, D, seed, b):
     yf = a["ctx"].apply_heff(b, x, precision=g.MIXED_BF16X3)
     yt = t["ctx"].apply_heff(b, x, precision=g.MIXED_BF16X3)
     yc = a["ctx"].apply_heff(b, x, precision=g.BF16X3_TWO_PHASE)  # comparison form on the fused context
+    assert np.array_equal(yf, t["ctx"].apply_heff(b, x, precision=g.BF16X3_FUSED))  # and the other way round
     assert np.array_equal(y64, t["ctx"].apply_heff(b, x, precision=g.FP64))
     nrm = np.linalg.norm(y64)
     assert np.linalg.norm(yf - y64) <= 2e-5 * nrm
