@@ -1006,8 +1006,23 @@ __device__ __forceinline__ float pow2f(int e) {
 // work spreads over the whole GPU however unequal the operator blocks are.
 constexpr int kSplitUnits = 2048;
 
+// Two adjacent BF16 values: one 4-byte store where the address allows it.
+__device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
+    if ((reinterpret_cast<uintptr_t>(p) & 3) == 0) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
+    } else {
+        p[0] = a;
+        p[1] = b;
+    }
+}
+
+// MODE 0: BF16x3 planes, MODE 1: sliced planes, MODE 2: both from one read
+// of the source (blocks: the BF16x3 destinations, blocks2: the sliced ones,
+// descriptor i of both over the same source units).  Lane gl of a group
+// handles columns c0 + 2 gl and c0 + 2 gl + 1 of its unit (ldd is a
+// multiple of 8, so both are valid or neither).
 template <int MODE>
-__global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
+__global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDesc* __restrict__ blocks2) {
     const SplitDesc b = blocks[blockIdx.x];
     const int nb64 = (b.ldd + 63) >> 6;
     const int G = b.ldd > 16 ? 32 : (b.ldd > 8 ? 16 : 8);
@@ -1016,35 +1031,41 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
     const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
     const int nw = blockDim.x >> 5;
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.src);
+    // destination row offset of source row r of a descriptor (regrouped rows: block rows < 2^31)
+    auto dest = [](const SplitDesc& d, int r) {
+        const long long ra = d.rbase + r;
+        if (d.lpitch != 0) {
+            const int t = int(ra) / int(d.R);
+            return d.dst + (long long)t * d.lpitch + (ra - (long long)t * d.R) * d.rpitch;
+        }
+        return d.dst + ra * d.rpitch;
+    };
     for (int u0 = (threadIdx.x >> 5) * upw; u0 < units; u0 += nw * upw) {
         const int u = u0 + sub;
         const bool uv = u < units;
         const int r = uv ? u / nb64 : 0;
         const int c0 = uv ? (u - r * nb64) * 64 : 0;
+        const int c = c0 + 2 * gl;
+        const bool cv = uv && c < c0 + 64 && c < b.ldd;
         unsigned long long bits[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = c0 + gl + G * h;
-            bits[h] = (uv && c < b.cols && c < c0 + 64) ? src[r * b.rs + (long long)c * b.cs] : 0ULL;
-        }
-        const long long ra = b.rbase + r;
-        long long doff = ra * b.rpitch;
-        if (b.lpitch != 0) {  // regrouped rows (block rows < 2^31)
-            const int t = int(ra) / int(b.R);
-            doff = (long long)t * b.lpitch + (ra - (long long)t * b.R) * b.rpitch;
-        }
-        __nv_bfloat16* d = b.dst + doff;
-        if constexpr (MODE == 0) {
+        for (int h = 0; h < 2; ++h) bits[h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
+        if constexpr (MODE == 0 || MODE == 2) {
+            if (cv) {
+                __nv_bfloat16 hi[2], lo[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + gl + G * h;
-                if (!uv || c >= b.ldd || c >= c0 + 64) continue;
-                const float f = __double2float_rn(__longlong_as_double((long long)bits[h]));
-                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-                d[c] = hi;
-                d[b.plane + c] = __float2bfloat16_rn(f - __bfloat162float(hi));
+                for (int h = 0; h < 2; ++h) {
+                    const float f = __double2float_rn(__longlong_as_double((long long)bits[h]));
+                    hi[h] = __float2bfloat16_rn(f);
+                    lo[h] = __float2bfloat16_rn(f - __bfloat162float(hi[h]));
+                }
+                __nv_bfloat16* d = dest(b, r) + c;
+                store_pair(d, hi[0], hi[1]);
+                store_pair(d + b.plane, lo[0], lo[1]);
             }
-        } else {
+        }
+        if constexpr (MODE == 1 || MODE == 2) {
+            const SplitDesc& e = MODE == 2 ? blocks2[blockIdx.x] : b;
             // block maximum: non-negative doubles order like their bit patterns
             const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFULL;
             unsigned long long mag = max(bits[0] & kAbs, bits[1] & kAbs);
@@ -1054,33 +1075,37 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks) {
             }
             const int emax = int(mag >> 52);  // biased exponent of the maximum
             const int ex = emax - 1022;       // max < 2^ex
-            float sc[4];
+            if (cv) {
+                float sc[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
+                for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
+                __nv_bfloat16 sl[4][2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + gl + G * h;
-                if (!uv || c >= b.ldd || c >= c0 + 64) continue;
-                const unsigned long long w = bits[h];
-                const int E = int((w >> 52) & 0x7FF);
-                long long q = 0;
-                if (emax > 0 && E > 0) {
-                    // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
-                    const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-                    const int sh = 21 + (emax - E);
-                    q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
-                    if (w >> 63) q = -q;
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned long long w = bits[h];
+                    const int E = int((w >> 52) & 0x7FF);
+                    long long q = 0;
+                    if (emax > 0 && E > 0) {
+                        // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
+                        const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+                        const int sh = 21 + (emax - E);
+                        q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
+                        if (w >> 63) q = -q;
+                    }
+                    const long long m1 = (q + (1LL << 23)) >> 24;
+                    long long rem = q - (m1 << 24);
+                    const long long m2 = (rem + (1LL << 15)) >> 16;
+                    rem -= m2 << 16;
+                    const long long m3 = (rem + (1LL << 7)) >> 8;
+                    const long long m4 = rem - (m3 << 8);
+                    sl[0][h] = __float2bfloat16_rn(float(m1) * sc[0]);
+                    sl[1][h] = __float2bfloat16_rn(float(m2) * sc[1]);
+                    sl[2][h] = __float2bfloat16_rn(float(m3) * sc[2]);
+                    sl[3][h] = __float2bfloat16_rn(float(m4) * sc[3]);
                 }
-                const long long m1 = (q + (1LL << 23)) >> 24;
-                long long rem = q - (m1 << 24);
-                const long long m2 = (rem + (1LL << 15)) >> 16;
-                rem -= m2 << 16;
-                const long long m3 = (rem + (1LL << 7)) >> 8;
-                const long long m4 = rem - (m3 << 8);
-                d[c] = __float2bfloat16_rn(float(m1) * sc[0]);
-                d[b.plane + c] = __float2bfloat16_rn(float(m2) * sc[1]);
-                d[2 * b.plane + c] = __float2bfloat16_rn(float(m3) * sc[2]);
-                d[3 * b.plane + c] = __float2bfloat16_rn(float(m4) * sc[3]);
+                __nv_bfloat16* d = dest(e, r) + c;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) store_pair(d + k * e.plane, sl[k][0], sl[k][1]);
             }
         }
     }
@@ -1386,24 +1411,29 @@ void tune_begin(Ctx& C) {
     }
 }
 
-// Operator slice planes of one product form for one side (0: O^Lx, 1:
-// O^xR), split from the FP64 enlarged arena of that side.
-template <int MODE> void build_ops(Ctx& C, int side) {
-    constexpr int NS = ModeCfg<MODE>::NS;
+// Operator slice planes for one side (0: O^Lx, 1: O^xR), split from the FP64
+// enlarged arena of that side: FORM 0 the BF16x3 planes, FORM 1 the sliced
+// planes, FORM 2 both in one pass over the FP64 arena.
+template <int FORM> void build_ops(Ctx& C, int side) {
     Heff& H = C.H;
-    TcPlan& P = H.tc.pl[MODE];
     cudaStream_t st = C.cs;
     const OpSet& O = side == 0 ? H.OL : H.OR;
     GBD_REQUIRE(O.resident(), GBD_ERR_STATE, "enlarged operators not resident for the operator planes");
     std::vector<std::vector<long long>> off;
     const long long n = std::max(op_layout(O, off), 8LL);
-    DevBuf& dst = side == 0 ? P.ol : P.orr;
-    (side == 0 ? P.nL : P.nR) = n;
-    dst.ensure_cached(size_t(n) * NS * 2, st);
-    // concat: layers side by side along each row ([row][layer][col]), the
-    // BF16x3 phase-2 B operand; otherwise layer-stacked rows
-    const bool concat = MODE == 0 && side == 1;
-    std::vector<SplitDesc> sd;
+    constexpr int mlo = FORM == 1 ? 1 : 0, mhi = FORM == 0 ? 0 : 1;  // the forms built
+    const int NSm[2] = {ModeCfg<0>::NS, ModeCfg<1>::NS};
+    __nv_bfloat16* dst[2] = {nullptr, nullptr};
+    for (int m = mlo; m <= mhi; ++m) {
+        TcPlan& P = H.tc.pl[m];
+        DevBuf& d = side == 0 ? P.ol : P.orr;
+        (side == 0 ? P.nL : P.nR) = n;
+        d.ensure_cached(size_t(n) * NSm[m] * 2, st);
+        dst[m] = d.as<__nv_bfloat16>();
+    }
+    // BF16x3 O^xR: layers side by side along each row ([row][layer][col]),
+    // the phase-2 B operand; otherwise layer-stacked rows
+    std::vector<SplitDesc> sd[2];
     for (size_t c = 0; c < O.cls.size(); ++c)
         for (size_t i = 0; i < O.cls[c].blocks.size(); ++i) {
             const OpBlock& b = O.cls[c].blocks[i];
@@ -1411,26 +1441,38 @@ template <int MODE> void build_ops(Ctx& C, int side) {
             const long long rows = Tn * b.rows;
             const int ldd = pad8(b.cols);
             const long long per = std::max<long long>(1, kSplitUnits / ((ldd + 63) / 64));
-            for (long long r0 = 0; r0 < rows; r0 += per) {
-                SplitDesc q{O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
-                            b.cols, ldd, dst.as<__nv_bfloat16>() + off[c][i], n, 1LL << 62, 0, ldd, r0};
-                if (concat) { q.R = std::max(b.rows, 1); q.lpitch = ldd; q.rpitch = Tn * ldd; }
-                sd.push_back(q);
-            }
+            for (long long r0 = 0; r0 < rows; r0 += per)
+                for (int m = mlo; m <= mhi; ++m) {
+                    SplitDesc q{O.data.as<double>() + b.off + r0 * b.cols, b.cols, 1, std::min(per, rows - r0),
+                                b.cols, ldd, dst[m] + off[c][i], n, 1LL << 62, 0, ldd, r0};
+                    if (m == 0 && side == 1) { q.R = std::max(b.rows, 1); q.lpitch = ldd; q.rpitch = Tn * ldd; }
+                    sd[m].push_back(q);
+                }
         }
-    if (!sd.empty()) {
-        DevBuf d;
-        upload_vec(d, sd, st);
-        for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
-            const unsigned nb = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
-            split_kernel<MODE><<<nb, 256, 0, st>>>(d.as<SplitDesc>() + i0);
+    if (!sd[mlo].empty()) {
+        DevBuf d0, d1;
+        upload_vec(d0, sd[mlo], st);
+        if (FORM == 2) upload_vec(d1, sd[1], st);
+        for (size_t i0 = 0; i0 < sd[mlo].size(); i0 += (1u << 30)) {
+            const unsigned nb = unsigned(std::min<size_t>(1u << 30, sd[mlo].size() - i0));
+            split_kernel<FORM><<<nb, 256, 0, st>>>(d0.as<SplitDesc>() + i0,
+                                                   FORM == 2 ? d1.as<SplitDesc>() + i0 : nullptr);
             count_launch();
         }
         GBD_CHECK_CUDA(cudaGetLastError());
-        GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffer is freed on return
+        GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffers are freed on return
     }
-    P.bytes_ops = double(P.nL + P.nR) * NS * 2.0;
-    (side == 0 ? P.ops_l : P.ops_r) = true;
+    for (int m = mlo; m <= mhi; ++m) {
+        TcPlan& P = H.tc.pl[m];
+        P.bytes_ops = double(P.nL + P.nR) * NSm[m] * 2.0;
+        (side == 0 ? P.ops_l : P.ops_r) = true;
+    }
+}
+
+// Both forms' operator planes are needed at this position: the mixed
+// Davidson with sliced anchors (which also renormalise from the sliced planes).
+bool both_forms(const Ctx& C) {
+    return C.cfg.precision == GBD_MIXED_BF16X3 && C.cfg.mixed_polish == 2;
 }
 
 // Split-K work list over the output sector tiles: per tile (BM x TBN) the K
@@ -1575,8 +1617,13 @@ template <int MODE> void build_plan(Ctx& C) {
     cudaStream_t st = C.cs;
     const double t0 = wall_ms();
     // ---- operator slice planes (already built when the FP64 arenas were released)
-    if (!P.ops_l) build_ops<MODE>(C, 0);
-    if (!P.ops_r) build_ops<MODE>(C, 1);
+    for (int side = 0; side < 2; ++side) {
+        if (P.ops(side)) continue;
+        // one pass writes both forms' planes when both are needed and the
+        // other form's are not there yet
+        if (both_forms(C) && !T.pl[1 - MODE].ops(side)) build_ops<2>(C, side);
+        else build_ops<MODE>(C, side);
+    }
     std::vector<std::vector<long long>> offL, offR;
     op_layout(H.OL, offL);
     op_layout(H.OR, offR);
@@ -1788,8 +1835,12 @@ void tc_prepare(Ctx& C, int mode) {
         heff_diag(C);  // the diagonal reads the FP64 arenas
         const double t0 = wall_ms();
         for (int side = 0; side < 2; ++side) {
-            if (!T.pl[0].ops(side)) build_ops<0>(C, side);
-            if (!T.pl[1].ops(side)) build_ops<1>(C, side);
+            if (!T.pl[0].ops(side) && !T.pl[1].ops(side)) {
+                build_ops<2>(C, side);
+            } else {
+                if (!T.pl[0].ops(side)) build_ops<0>(C, side);
+                if (!T.pl[1].ops(side)) build_ops<1>(C, side);
+            }
             (side == 0 ? H.OL : H.OR).data.release();
         }
         C.timers[Ctx::T_PREP_SPLIT] += wall_ms() - t0;
@@ -1877,7 +1928,7 @@ template <int MODE> void run_plan(Ctx& C) {
     TcPlan& P = T.pl[MODE];
     cudaStream_t st = C.cs;
     if (P.n_psi > 0) {
-        split_kernel<MODE><<<unsigned(P.n_psi), 256, 0, st>>>(P.psi_split.as<SplitDesc>());
+        split_kernel<MODE><<<unsigned(P.n_psi), 256, 0, st>>>(P.psi_split.as<SplitDesc>(), nullptr);
         count_launch();
     }
     if (P.n_w1 > 0) {
@@ -1960,7 +2011,7 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
     DevBuf dsd;
     upload_vec(dsd, sd, st);
     if (!sd.empty()) {
-        split_kernel<1><<<unsigned(sd.size()), 256, 0, st>>>(dsd.as<SplitDesc>());
+        split_kernel<1><<<unsigned(sd.size()), 256, 0, st>>>(dsd.as<SplitDesc>(), nullptr);
         count_launch();
     }
     std::vector<CUtensorMap> maps;
@@ -2081,7 +2132,7 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
     upload_vec(dsdB, sdB, st);
     for (size_t i0 = 0; i0 < sdB.size(); i0 += (1u << 30)) {
         const unsigned n = unsigned(std::min<size_t>(1u << 30, sdB.size() - i0));
-        split_kernel<1><<<n, 256, 0, st>>>(dsdB.as<SplitDesc>() + i0);
+        split_kernel<1><<<n, 256, 0, st>>>(dsdB.as<SplitDesc>() + i0, nullptr);
         count_launch();
     }
     if (!worksB.empty()) {
@@ -2147,7 +2198,7 @@ void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::ve
     upload_vec(dsd, sd, st);
     for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
         const unsigned n = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
-        split_kernel<1><<<n, 256, 0, st>>>(dsd.as<SplitDesc>() + i0);
+        split_kernel<1><<<n, 256, 0, st>>>(dsd.as<SplitDesc>() + i0, nullptr);
         count_launch();
     }
     // tensor maps (one per distinct operand), segments, work items
