@@ -653,7 +653,7 @@ def run_ours(args, rank, world, local_rank):
                      "at_product_limit": sum(1 for x in status if x == 1),
                      "at_precision_floor": sum(1 for x in status if x == 2),
                      "status_note": "0: residual <= tol; 1: product limit; 2: mixed form stopped at its "
-                                    "rounding floor (an anchor that did not halve the exact residual, or six "
+                                    "rounding floor (an anchor that did not cut the exact residual by a fifth, or six "
                                     "anchors) above tol",
                      "status_per_step": status, "matvecs_per_step": [s["matvecs"] for s in stats],
                      "resid_per_step": [s["resid"] for s in stats],

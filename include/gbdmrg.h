@@ -59,8 +59,8 @@ enum {
     GBD_ERR_STATE = -7,        /* call out of order (e.g. no integrals loaded)   */
     GBD_WARN_NOT_CONVERGED = 1, /* Davidson hit its product limit                */
     GBD_WARN_PRECISION_FLOOR = 2 /* mixed Davidson: its anchors stopped above
-                                    dav_tol (an anchor that did not halve the
-                                    best exact residual, or GBD_MAX_ANCHORS of
+                                    dav_tol (an anchor that did not cut the
+                                    best exact residual by a fifth, or GBD_MAX_ANCHORS of
                                     them: the floor the BF16x3 products leave);
                                     the result is the anchored pair with the
                                     smallest exact residual                    */

@@ -1376,8 +1376,10 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
                 best_theta = theta;
             }
             // the mixed products' rounding floor: an anchor round that does not
-            // halve the best exact residual, or the last allowed anchor
-            if (anchors >= GBD_MAX_ANCHORS || (prev_best >= 0.0 && rn > 0.5 * prev_best)) {
+            // cut the best exact residual by a fifth, or the last allowed
+            // anchor (far from convergence, with a small gap, rounds are
+            // slower but still gain; at the floor they gain nothing)
+            if (anchors >= GBD_MAX_ANCHORS || (prev_best >= 0.0 && rn > 0.8 * prev_best)) {
                 status = GBD_WARN_PRECISION_FLOOR;
                 break;
             }

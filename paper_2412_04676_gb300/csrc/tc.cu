@@ -116,6 +116,16 @@ __device__ __forceinline__ void tma_4d(uint32_t dst, const void* map, int c0, in
         : "memory");
 }
 
+// TMA tile store shared -> global (bulk group of the issuing thread)
+__device__ __forceinline__ void tma_store_4d(const void* map, uint32_t src, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     uint64_t d = 0;
@@ -481,9 +491,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 const int et = threadIdx.x - 64;  // 0 .. EPI_THREADS - 1
                 constexpr int vpr = K_::BN / 8;   // 16-byte vectors per row
                 if constexpr (MODE == 0) {
-                    // BF16 hi / lo through two staging planes (16-byte
-                    // vectors XOR-swizzled by row), then coalesced 16-byte
-                    // stores of whole rows
+                    // BF16 hi / lo through four staging tiles (plane x 64-column
+                    // half, 128 rows of 128 bytes in the TMA 128-byte swizzle:
+                    // chunk c of row r at chunk c ^ (r & 7)).  The rows of the
+                    // tile's first layer go out as four TMA tile stores (rows
+                    // past the layer's end fall outside the store map and are
+                    // not written); rows of later layers (sectors shorter than
+                    // the tile) are stored by the epilogue threads.
                     uint32_t ph[CP / 2], pl[CP / 2];
 #pragma unroll
                     for (int i = 0; i < CP; i += 2) {
@@ -496,42 +510,53 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                         ph[i / 2] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
                         pl[i / 2] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
                     }
+                    constexpr int SUB = BM * 128;  // one staging tile: 128 rows x 64 BF16
+                    auto soff = [](int r, int v) {  // byte offset of 16-byte vector v (0..15) of row r in plane 0
+                        return (v >> 3) * SUB + r * 128 + (((v & 7) ^ (r & 7)) << 4);
+                    };
+                    if (et == 0) bulk_wait_read();  // the previous tile's stores have read the staging tiles
                     asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");  // earlier readers are done
 #pragma unroll
                     for (int j = 0; j < CP / 8; ++j) {
-                        const int v = part * (CP / 8) + j;
-                        const int off = row * K_::RS + ((v ^ (row & (vpr - 1))) << 4);
+                        const int off = soff(row, part * (CP / 8) + j);
                         *reinterpret_cast<uint4*>(epi + off) = make_uint4(ph[4 * j], ph[4 * j + 1], ph[4 * j + 2], ph[4 * j + 3]);
-                        *reinterpret_cast<uint4*>(epi + BM * K_::RS + off) =
+                        *reinterpret_cast<uint4*>(epi + 2 * SUB + off) =
                             make_uint4(pl[4 * j], pl[4 * j + 1], pl[4 * j + 2], pl[4 * j + 3]);
                     }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the TMA unit
                     asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-                    // thread et copies vector et % vpr of rows et / vpr + k * rstep;
-                    // with layer-concatenated output, row t * lay_rows + rr goes
-                    // to row rr at column offset t * lay_pitch
+                    // rows of the first layer: [0, kfirst)
+                    const int t0 = w.m0 / w.lay_rows, lo0 = w.m0 - t0 * w.lay_rows;
+                    const int kfirst = min(BM, w.lay_rows - lo0);
+                    if (et == 0) {
+                        const CUtensorMap* om = maps + w.omap;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                if (w.n0 + h * 64 < w.colcap)
+                                    tma_store_4d(om, smem_u32(epi + (2 * q + h) * SUB), w.n0 + h * 64, t0, lo0, q);
+                        bulk_commit();
+                    }
+                    // later layers: thread et copies vector et % vpr of rows
+                    // kfirst + et / vpr + k * rstep; stacked row t * lay_rows + rr
+                    // goes to row rr at column offset t * lay_pitch
                     constexpr int rstep = EPI_THREADS / vpr;
                     const int cv = et % vpr;
                     const int gcol = w.n0 + cv * 8;
-                    int r = et / vpr;
+                    int r = kfirst + et / vpr;
                     int grow = w.m0 + r;
-                    int t = 0, rr = grow;
-                    if (w.lay_rows > 0) {
-                        t = grow / w.lay_rows;
-                        rr = grow - t * w.lay_rows;
-                    }
+                    int t = grow / w.lay_rows, rr = grow - t * w.lay_rows;
                     for (; r < BM; r += rstep) {
                         if (grow < w.M && gcol < w.colcap) {
-                            const long long at = w.lay_rows > 0 ? (long long)rr * ldo + (long long)t * w.lay_pitch + gcol
-                                                                : (long long)grow * ldo + gcol;
-                            const int so = r * K_::RS + ((cv ^ (r & (vpr - 1))) << 4);
+                            const long long at = (long long)rr * ldo + (long long)t * w.lay_pitch + gcol;
+                            const int so = soff(r, cv);
                             *reinterpret_cast<uint4*>(o0 + at) = *reinterpret_cast<const uint4*>(epi + so);
-                            *reinterpret_cast<uint4*>(o0 + w.plane + at) = *reinterpret_cast<const uint4*>(epi + BM * K_::RS + so);
+                            *reinterpret_cast<uint4*>(o0 + w.plane + at) = *reinterpret_cast<const uint4*>(epi + 2 * SUB + so);
                         }
                         grow += rstep;
-                        if (w.lay_rows > 0) {
-                            rr += rstep;
-                            while (rr >= w.lay_rows) { rr -= w.lay_rows; ++t; }
-                        }
+                        rr += rstep;
+                        while (rr >= w.lay_rows) { rr -= w.lay_rows; ++t; }
                     }
                 } else {
                     // four slices on the grid of this row's maximum over the
@@ -593,6 +618,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             }
         }
     }
+    // the phase-1 tile stores have landed before the CTA exits
+    if (PH == 1 && MODE == 0 && threadIdx.x == 64) bulk_wait_all();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
@@ -1040,16 +1067,32 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDe
         }
         return d.dst + ra * d.rpitch;
     };
-    for (int u0 = (threadIdx.x >> 5) * upw; u0 < units; u0 += nw * upw) {
-        const int u = u0 + sub;
+    // kInflight units per lane group and iteration: all their loads are
+    // issued before any is processed, so each warp keeps several 512-byte
+    // row segments in flight
+    constexpr int kInflight = 4;
+    for (int ub = (threadIdx.x >> 5) * upw * kInflight; ub < units; ub += nw * upw * kInflight) {
+      unsigned long long bw[kInflight][2];
+#pragma unroll
+      for (int f = 0; f < kInflight; ++f) {
+        const int u = ub + f * upw + sub;
         const bool uv = u < units;
         const int r = uv ? u / nb64 : 0;
         const int c0 = uv ? (u - r * nb64) * 64 : 0;
         const int c = c0 + 2 * gl;
         const bool cv = uv && c < c0 + 64 && c < b.ldd;
-        unsigned long long bits[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) bits[h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
+        for (int h = 0; h < 2; ++h) bw[f][h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
+      }
+#pragma unroll
+      for (int f = 0; f < kInflight; ++f) {
+        const int u = ub + f * upw + sub;
+        const bool uv = u < units;
+        const int r = uv ? u / nb64 : 0;
+        const int c0 = uv ? (u - r * nb64) * 64 : 0;
+        const int c = c0 + 2 * gl;
+        const bool cv = uv && c < c0 + 64 && c < b.ldd;
+        const unsigned long long* bits = bw[f];
         if constexpr (MODE == 0 || MODE == 2) {
             if (cv) {
                 __nv_bfloat16 hi[2], lo[2];
@@ -1108,6 +1151,7 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDe
                 for (int k = 0; k < 4; ++k) store_pair(d + k * e.plane, sl[k][0], sl[k][1]);
             }
         }
+      }
     }
 }
 
@@ -1719,6 +1763,14 @@ template <int MODE> void build_plan(Ctx& C) {
         int mA = add_maps(P.ol.as<__nv_bfloat16>() + ol, P.nL, mLi, (long long)Tn * mLo, 0, pad8(mLi), 0, BM);
         int sidx = int(s1.size());
         s1.push_back({mA, psi_map[p.si], 0, 0, mLi, 1, 2, (mLi + BK - 1) / BK});
+        int xmap = -1;
+        if (MODE == 0) {
+            // tile stores of X ([row][layer][col]): dims (col, layer, row), box 64 x 1 x 128
+            const long long dx[2] = {Tn, mLo}, sx[2] = {pad8(mRi), (long long)Tn * pad8(mRi)};
+            const int bx[2] = {1, BM};
+            xmap = int(maps.size());
+            maps.push_back(make_map_n(xbase + p.x, pad8(mRi), 2, dx, sx, bx, NS, P.nx));
+        }
         for (long long m0 = 0; m0 < (long long)Tn * mLo; m0 += BM)
             for (int n0 = 0; n0 < mRi; n0 += TBN) {
                 Work w{};
@@ -1743,6 +1795,7 @@ template <int MODE> void build_plan(Ctx& C) {
                     w.ldo = pad8(mRi);
                 }
                 w.out = xbase + p.x;
+                w.omap = xmap;
                 w1.push_back(w);
             }
         seg_of_out[p.so].push_back(int(s2.size()));

@@ -75,6 +75,7 @@ struct Work {
     // kind 2: column e of a row goes to (e / ncols) * ldr + e % ncols (ncols = 0: e)
     int ncols;
     long long ldr;
+    int omap;          // kind 1, BF16x3: tensor map of the output X for the tile stores
     void* out;
 };
 

@@ -79,7 +79,7 @@ def test_davidson_product_limit_is_a_warning():
 
 def test_mixed_davidson_reports_its_precision_floor():
     # a tolerance below what the anchor products can resolve: once an anchor
-    # no longer halves the exact residual the mixed Davidson stops and says so
+    # no longer cuts the exact residual by a fifth the mixed Davidson stops and says so
     # (the result is its best anchored pair)
     L, N, D, b = 8, 8, 24, 3
     h, eri = inputs.make_integrals(L, 45)
