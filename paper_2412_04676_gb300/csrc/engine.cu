@@ -146,14 +146,92 @@ std::unique_ptr<OpSet> trivial_env(Ctx& C, int side) {
     return E;
 }
 
-// dense layer-to-layer coefficient matrix between an input and an output class
-struct Link {
-    int ci, co, s, t;
-    std::vector<double> W;  // T_in x T_out
-    long long doff = 0;
-};
-
 }  // namespace
+
+// Links of the enlargement (side, cut k) into the output classes of `out`,
+// built on first use (they depend only on the MPO and the classes).
+static const EnlLinks& enl_links(Ctx& C, const OpSet& Ein, int side, int k, const OpSet& out) {
+    auto& cache = C.enl_links[side];
+    if (int(cache.size()) < C.L + 1) cache.resize(C.L + 1);
+    EnlLinks& LK = cache[k];
+    if (LK.built) return LK;
+    const Mpo& M = C.mpo;
+    // links between an input class and an output class for one local matrix
+    // element (s, t), collected as sparse entries first
+    std::map<std::tuple<int, int, int, int>, int> link_id;
+    std::vector<EnlLink>& links = LK.links;
+    std::vector<std::vector<std::tuple<int, int, double>>> ents;  // (input layer, output layer, value)
+    for (const auto& e : M.W[k]) {
+        int sin = side == 0 ? e.a : e.c;
+        int sout = side == 0 ? e.c : e.a;
+        if (sin >= (int)Ein.state_class.size()) continue;
+        int ci = Ein.state_class[sin];
+        if (ci < 0) continue;
+        int li = Ein.state_layer[sin];
+        int co = out.state_class[sout], lo = out.state_layer[sout];
+        auto key = std::make_tuple(ci, co, e.s, e.t);
+        auto it = link_id.find(key);
+        int id;
+        if (it == link_id.end()) {
+            id = int(links.size());
+            link_id[key] = id;
+            EnlLink L;
+            L.ci = ci; L.co = co; L.s = e.s; L.t = e.t;
+            links.push_back(std::move(L));
+            ents.emplace_back();
+        } else {
+            id = it->second;
+        }
+        ents[id].emplace_back(li, lo, e.v);
+    }
+    // a link whose output layers each take few input layers is a set of
+    // scaled copy-sums; the rest (complementary sums over many normal
+    // operators) are dense coefficient GEMMs.  With GB300's narrow FP64 pipe
+    // a dense GEMM over T_in layers costs T_in FMAs per element, a copy-sum
+    // one load per nonzero.
+    constexpr int kMaxCopySources = 32;
+    LK.sparse.assign(links.size(), 1);
+    LK.link_col0.assign(links.size(), -1);
+    LK.amax.assign(links.size(), 0);
+    long long wtot = 0;
+    for (size_t i = 0; i < links.size(); ++i) {
+        const int Tin = int(Ein.cls[links[i].ci].states.size());
+        const int Tout = int(out.cls[links[i].co].states.size());
+        std::vector<int> cnt(Tout, 0);
+        for (const auto& x : ents[i]) ++cnt[std::get<1>(x)];
+        for (int c = 0; c < Tout; ++c)
+            if (cnt[c] > kMaxCopySources) { LK.sparse[i] = 0; break; }
+        if (LK.sparse[i]) {
+            std::vector<std::vector<std::pair<int, double>>> cs(Tout);
+            for (const auto& x : ents[i]) {
+                auto& v = cs[std::get<1>(x)];
+                bool merged = false;
+                for (auto& av : v)
+                    if (av.first == std::get<0>(x)) { av.second += std::get<2>(x); merged = true; }
+                if (!merged) v.push_back({std::get<0>(x), std::get<2>(x)});
+            }
+            LK.link_col0[i] = int(LK.ccols.size());
+            for (const auto& v : cs) {
+                LK.ccols.push_back({int(LK.ccoefs.size()), int(v.size())});
+                for (const auto& av : v) {
+                    LK.ccoefs.push_back({av.first, av.second});
+                    LK.amax[i] = std::max(LK.amax[i], av.first);
+                }
+            }
+        } else {
+            links[i].W.assign(size_t(Tin) * Tout, 0.0);
+            for (const auto& x : ents[i]) links[i].W[size_t(std::get<0>(x)) * Tout + std::get<1>(x)] += std::get<2>(x);
+            links[i].doff = wtot;
+            wtot += (long long)links[i].W.size();
+        }
+        LK.by_cst[std::make_tuple(links[i].co, links[i].s, links[i].t)].push_back(int(i));
+    }
+    LK.wall.assign(size_t(std::max<long long>(wtot, 1)), 0.0);
+    for (size_t i = 0; i < links.size(); ++i)
+        if (!LK.sparse[i]) std::copy(links[i].W.begin(), links[i].W.end(), LK.wall.begin() + links[i].doff);
+    LK.built = true;
+    return LK;
+}
 
 // ============================================================== enlargement
 // Pre-processing (Sec. II.B step 1): the operators of the enlarged block.
@@ -172,72 +250,11 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     make_classes(M.dq[out_cut], out);
     GBD_REQUIRE(Ein.resident(), GBD_ERR_STATE, "environment not resident on the device");
 
-    // links between an input class and an output class for one local matrix
-    // element (s, t), collected as sparse entries first
-    std::map<std::tuple<int, int, int, int>, int> link_id;
-    std::vector<Link> links;
-    std::vector<std::vector<std::tuple<int, int, double>>> ents;  // (input layer, output layer, value)
-    for (const auto& e : M.W[k]) {
-        int sin = side == 0 ? e.a : e.c;
-        int sout = side == 0 ? e.c : e.a;
-        if (sin >= (int)Ein.state_class.size()) continue;
-        int ci = Ein.state_class[sin];
-        if (ci < 0) continue;
-        int li = Ein.state_layer[sin];
-        int co = out.state_class[sout], lo = out.state_layer[sout];
-        auto key = std::make_tuple(ci, co, e.s, e.t);
-        auto it = link_id.find(key);
-        int id;
-        if (it == link_id.end()) {
-            id = int(links.size());
-            link_id[key] = id;
-            Link L;
-            L.ci = ci; L.co = co; L.s = e.s; L.t = e.t;
-            links.push_back(std::move(L));
-            ents.emplace_back();
-        } else {
-            id = it->second;
-        }
-        ents[id].emplace_back(li, lo, e.v);
-    }
-    // a link whose output layers each take few input layers is a set of
-    // scaled copy-sums; the rest (complementary sums over many normal
-    // operators) are dense coefficient GEMMs.  With GB300's narrow FP64 pipe
-    // a dense GEMM over T_in layers costs T_in FMAs per element, a copy-sum
-    // one load per nonzero.
-    constexpr int kMaxCopySources = 32;
-    std::vector<char> sparse(links.size(), 1);
-    std::vector<std::vector<std::vector<std::pair<int, double>>>> col_src(links.size());
-    for (size_t i = 0; i < links.size(); ++i) {
-        const int Tin = int(Ein.cls[links[i].ci].states.size());
-        const int Tout = int(out.cls[links[i].co].states.size());
-        std::vector<int> cnt(Tout, 0);
-        for (const auto& x : ents[i]) ++cnt[std::get<1>(x)];
-        for (int c = 0; c < Tout; ++c)
-            if (cnt[c] > kMaxCopySources) { sparse[i] = 0; break; }
-        if (sparse[i]) {
-            auto& cs = col_src[i];
-            cs.assign(Tout, {});
-            for (const auto& x : ents[i]) {
-                auto& v = cs[std::get<1>(x)];
-                bool merged = false;
-                for (auto& av : v)
-                    if (av.first == std::get<0>(x)) { av.second += std::get<2>(x); merged = true; }
-                if (!merged) v.push_back({std::get<0>(x), std::get<2>(x)});
-            }
-        } else {
-            links[i].W.assign(size_t(Tin) * Tout, 0.0);
-            for (const auto& x : ents[i]) links[i].W[size_t(std::get<0>(x)) * Tout + std::get<1>(x)] += std::get<2>(x);
-        }
-    }
+    const EnlLinks& LK = enl_links(C, Ein, side, k, out);
+    const std::vector<EnlLink>& links = LK.links;
+    const std::vector<char>& sparse = LK.sparse;
+    const auto& by_cst = LK.by_cst;
     const double t_links = wall_ms();
-    std::map<std::tuple<int, int, int>, std::vector<int>> by_cst;  // (co, s, t) -> links
-    long long wtot = 0;
-    for (size_t i = 0; i < links.size(); ++i) {
-        by_cst[std::make_tuple(links[i].co, links[i].s, links[i].t)].push_back(int(i));
-        links[i].doff = wtot;
-        if (!sparse[i]) wtot += (long long)links[i].W.size();
-    }
     // output blocks and their sub-block tasks
     struct Sub {
         int cls, blk;
@@ -273,9 +290,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     const double t_subs = wall_ms();
     alloc_env_cached(C, out);
     // upload coefficient matrices of the dense links
-    std::vector<double> wall(size_t(std::max<long long>(wtot, 1)));
-    for (size_t i = 0; i < links.size(); ++i)
-        if (!sparse[i]) std::copy(links[i].W.begin(), links[i].W.end(), wall.begin() + links[i].doff);
+    const std::vector<double>& wall = LK.wall;
     C.scratch_w.ensure(wall.size() * sizeof(double));
     GBD_CHECK_CUDA(cudaMemcpyAsync(C.scratch_w.p, wall.data(), wall.size() * sizeof(double), cudaMemcpyHostToDevice, C.cs));
     const double* dW = C.scratch_w.as<double>();
@@ -285,18 +300,11 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
     P.clear();
     std::vector<CopyItem> items;
     std::vector<CopyLink> clinks;
-    std::vector<CopyCol> ccols;
-    std::vector<CopyCoef> ccoefs;
+    std::vector<int> clink_amax;  // largest input layer each copy link reads (bounds check)
     // per sparse link, its (input layer, coefficient) lists per output layer
-    std::vector<int> link_col0(links.size(), -1);
-    for (size_t i = 0; i < links.size(); ++i) {
-        if (!sparse[i]) continue;
-        link_col0[i] = int(ccols.size());
-        for (const auto& v : col_src[i]) {
-            ccols.push_back({int(ccoefs.size()), int(v.size())});
-            for (const auto& av : v) ccoefs.push_back({av.first, av.second});
-        }
-    }
+    const std::vector<CopyCol>& ccols = LK.ccols;
+    const std::vector<CopyCoef>& ccoefs = LK.ccoefs;
+    const std::vector<int>& link_col0 = LK.link_col0;
     int max_tout = 0;
     // mixed form: the dense coefficient GEMMs run on the tensor cores in the
     // sliced form (FP64 GEMMs otherwise)
@@ -322,7 +330,7 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         const int tc_seg0 = int(tc_segs.size());
         std::vector<std::pair<int, const OpBlock*>> sp;  // sparse links of this sub-block
         for (auto& pr : sub.src) {
-            const Link& L = links[pr.first];
+            const EnlLink& L = links[pr.first];
             const OpClass& ic = Ein.cls[L.ci];
             const OpBlock& ib = ic.blocks[pr.second];
             if (sparse[pr.first]) {
@@ -352,14 +360,18 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         if (sp.empty()) continue;
         CopyItem it{};
         it.dst = dsub;
+        // a sub-block no coefficient GEMM wrote is still zero from the allocation
+        it.overwrite = (segs.empty() && int(tc_segs.size()) == tc_seg0) ? 1 : 0;
         it.out_pitch = (long long)ob.rows * ob.cols;
         it.ldr = ob.cols;
         it.rows = sub.rows;
         it.cols = sub.cols;
         it.tout = Tout;
         it.link0 = int(clinks.size());
-        for (const auto& lb : sp)
+        for (const auto& lb : sp) {
             clinks.push_back({din + lb.second->off, (long long)lb.second->rows * lb.second->cols, link_col0[lb.first]});
+            clink_amax.push_back(LK.amax[lb.first]);
+        }
         it.nlink = int(clinks.size()) - it.link0;
         items.push_back(it);
         max_tout = std::max(max_tout, Tout);
@@ -373,14 +385,11 @@ static void enlarge(Ctx& C, const OpSet& Ein, int side, int k, OpSet& out, EBasi
         const double* e = it.dst + (long long)(it.tout - 1) * it.out_pitch + (long long)(it.rows - 1) * it.ldr + it.cols;
         GBD_REQUIRE(it.dst >= dout && e <= dout + out.total, GBD_ERR_STATE, "enlarge: copy outside its block");
         for (int l = it.link0; l < it.link0 + it.nlink; ++l) {
+            // every copy of the link reads input layers 0..amax of its block
             const CopyLink& L = clinks[l];
-            const CopyCol* cc = ccols.data() + L.col0;
-            for (int c = 0; c < it.tout; ++c)
-                for (int k = cc[c].c0; k < cc[c].c0 + cc[c].n; ++k) {
-                    const double* a = L.src + (long long)ccoefs[k].a * L.in_pitch;
-                    GBD_REQUIRE(a >= din && a + (long long)it.rows * it.cols <= din + Ein.total, GBD_ERR_STATE,
-                                "enlarge: copy source outside the environment");
-                }
+            const double* a = L.src + (long long)clink_amax[l] * L.in_pitch;
+            GBD_REQUIRE(L.src >= din && a + (long long)it.rows * it.cols <= din + Ein.total, GBD_ERR_STATE,
+                        "enlarge: copy source outside the environment");
         }
     }
     const double t_dev0 = wall_ms();
@@ -650,6 +659,7 @@ void load_integrals(Ctx& C, int L, const double* h, const double* eri, double ec
     C.eri.assign(eri, eri + n4);
     C.ecore = ecore;
     C.mpo.build(L, h, eri, C.cfg.switch_cut);
+    for (auto& v : C.enl_links) v.clear();  // they follow the MPO
     C.have_ints = true;
     C.site_blocks_data.assign(L, {});
     C.site_blocks_meta.assign(L, {});

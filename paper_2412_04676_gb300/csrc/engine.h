@@ -4,7 +4,9 @@
 
 #include <cusolverDn.h>
 
+#include <map>
 #include <memory>
+#include <tuple>
 #include <vector>
 
 #include "core.h"
@@ -83,6 +85,28 @@ struct Heff {
     }
 };
 
+// The links of one enlargement (side, cut) between input and output operator
+// classes for each local matrix element, with their coefficients: copy-sum
+// lists for sparse links, dense coefficient matrices for the others.  They
+// depend only on the MPO (Eq. 1 split at the cut), so they are built once per
+// context and integrals, and reused by every sweep.
+struct EnlLink {
+    int ci, co, s, t;
+    std::vector<double> W;  // T_in x T_out (dense links)
+    long long doff = 0;     // offset of W in `wall`
+};
+struct EnlLinks {
+    bool built = false;
+    std::vector<EnlLink> links;
+    std::vector<char> sparse;
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_cst;  // (output class, s, t) -> links
+    std::vector<double> wall;       // dense coefficient matrices, concatenated
+    std::vector<int> link_col0;     // sparse link -> first CopyCol (output layer 0)
+    std::vector<int> amax;          // sparse link -> largest input layer its copies read
+    std::vector<CopyCol> ccols;
+    std::vector<CopyCoef> ccoefs;
+};
+
 struct Ctx {
     gbd_config cfg{};
     bool have_ints = false, cuda_ready = false;
@@ -98,6 +122,7 @@ struct Ctx {
     std::vector<std::unique_ptr<OpSet>> envL, envR;
     std::vector<HostEnv> hostL, hostR;
     std::unique_ptr<SpillStore> spill;   // created at the first spill
+    std::vector<EnlLinks> enl_links[2];  // per side and cut; cleared with the integrals
     size_t pinned_bytes = 0;             // packed-stream buffers of the host store
     unsigned long long io_stamp = 0;
     cudaStream_t cs = nullptr, ios = nullptr;

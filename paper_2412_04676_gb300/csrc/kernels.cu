@@ -372,7 +372,9 @@ __global__ void copy_sum_kernel(const CopyItem* __restrict__ items, const CopyLi
             }
             if (!any) continue;
             const int r = e / it.cols, cc = e - r * it.cols;
-            dst[(long long)r * it.ldr + cc] += v;
+            double* o = dst + (long long)r * it.ldr + cc;
+            if (it.overwrite) *o = v;  // no other writer: skip the read
+            else *o += v;
         }
     }
 }

@@ -159,6 +159,8 @@ struct CopyItem {
     long long ldr;
     int rows, cols, tout; // sub-block shape, output layers
     int link0, nlink;     // CopyLink range
+    int overwrite;        // 1: no GEMM writes this sub-block, so the copy-sum stores (the
+                          // arena is zero-filled) instead of adding to what is there
 };
 // grid: (items, ceil(max tout / kCopyLayers)); each (item, layer) has one writer
 constexpr int kCopyLayers = 8;
