@@ -1135,12 +1135,14 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDe
                         q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
                         if (w >> 63) q = -q;
                     }
-                    const long long m1 = (q + (1LL << 23)) >> 24;
-                    long long rem = q - (m1 << 24);
-                    const long long m2 = (rem + (1LL << 15)) >> 16;
+                    // |q| <= 2^32: the digits and every remainder after the
+                    // first fit in 32-bit integers
+                    const int m1 = int((q + (1LL << 23)) >> 24);
+                    int rem = int(q - ((long long)m1 << 24));
+                    const int m2 = (rem + (1 << 15)) >> 16;
                     rem -= m2 << 16;
-                    const long long m3 = (rem + (1LL << 7)) >> 8;
-                    const long long m4 = rem - (m3 << 8);
+                    const int m3 = (rem + (1 << 7)) >> 8;
+                    const int m4 = rem - (m3 << 8);
                     sl[0][h] = __float2bfloat16_rn(float(m1) * sc[0]);
                     sl[1][h] = __float2bfloat16_rn(float(m2) * sc[1]);
                     sl[2][h] = __float2bfloat16_rn(float(m3) * sc[2]);
