@@ -30,6 +30,7 @@
 #include <cstring>
 
 #include "engine.h"
+#include "split.h"
 #include "tc.h"
 
 namespace gbd {
@@ -998,165 +999,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fused_kernel(const Work* __rest
     }
 }
 
-// ------------------------------------------------------------------ helpers
-// Operand splitting.  Element (r, c) of the source is src[r * rs + c * cs];
-// columns from cols to ldd - 1 are zero padding; plane k of the output
-// starts at dst + k * plane.  A group of G lanes handles one (row, 64-column
-// block) unit (G = 32, or 8 / 16 for short rows, so a warp then covers
-// several rows).  GB300's FP64 pipe is narrow, so the per-element work is
-// integer and FP32 arithmetic on the FP64 bit patterns.
-// Output rows can be regrouped (a layer-stacked block stored with its layers
-// side by side along the row) through R, lpitch and rpitch.
-//   MODE 0: x = hi + lo, hi = bf16(f), lo = bf16(f - hi) with f = fp32(x)
-//     (|x - hi - lo| <= 2^-18 |x|).
-//   MODE 1: error-free slicing: with 2^(e-1) <= max |x| < 2^e over the unit,
-//     q = round(x 2^(32-e)) (|q| <= 2^32) is cut into balanced base-256
-//     digits q = m1 2^24 + m2 2^16 + m3 2^8 + m4 (|m1| <= 256, |mk| <= 128),
-//     and slice k = mk 2^(e - 8k) is exact in BF16; x = sum of the slices
-//     + O(2^(e-33)).  Units whose maximum is zero or subnormal are zero.
-struct SplitDesc {
-    const double* src;
-    long long rs, cs;
-    long long rows;
-    int cols, ldd;
-    __nv_bfloat16* dst;  // source row r goes to dst + (r / R) * lpitch + (r % R) * rpitch
-    long long plane;
-    long long R, lpitch, rpitch;
-    long long rbase;     // row index of src row 0 within the whole block (for the regrouping)
-};
-
-__device__ __forceinline__ float pow2f(int e) {
-    return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.f, e);
-}
-
-// One CTA per descriptor; descriptors cover at most kSplitUnits units, so the
-// work spreads over the whole GPU however unequal the operator blocks are.
-constexpr int kSplitUnits = 2048;
-
-// Two adjacent BF16 values: one 4-byte store where the address allows it.
-__device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
-    if ((reinterpret_cast<uintptr_t>(p) & 3) == 0) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
-    } else {
-        p[0] = a;
-        p[1] = b;
-    }
-}
-
-// MODE 0: BF16x3 planes, MODE 1: sliced planes, MODE 2: both from one read
-// of the source (blocks: the BF16x3 destinations, blocks2: the sliced ones,
-// descriptor i of both over the same source units).  Lane gl of a group
-// handles columns c0 + 2 gl and c0 + 2 gl + 1 of its unit (ldd is a
-// multiple of 8, so both are valid or neither).
-template <int MODE>
-__global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDesc* __restrict__ blocks2) {
-    const SplitDesc b = blocks[blockIdx.x];
-    const int nb64 = (b.ldd + 63) >> 6;
-    const int G = b.ldd > 16 ? 32 : (b.ldd > 8 ? 16 : 8);
-    const int upw = 32 / G;  // units per warp and iteration
-    const int units = int(b.rows) * nb64;  // a descriptor covers at most max(kSplitUnits, nb64) units
-    const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-    const int nw = blockDim.x >> 5;
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.src);
-    // destination row offset of source row r of a descriptor (regrouped rows: block rows < 2^31)
-    auto dest = [](const SplitDesc& d, int r) {
-        const long long ra = d.rbase + r;
-        if (d.lpitch != 0) {
-            const int t = int(ra) / int(d.R);
-            return d.dst + (long long)t * d.lpitch + (ra - (long long)t * d.R) * d.rpitch;
-        }
-        return d.dst + ra * d.rpitch;
-    };
-    // kInflight units per lane group and iteration: all their loads are
-    // issued before any is processed, so each warp keeps several 512-byte
-    // row segments in flight
-    constexpr int kInflight = 4;
-    for (int ub = (threadIdx.x >> 5) * upw * kInflight; ub < units; ub += nw * upw * kInflight) {
-      unsigned long long bw[kInflight][2];
-#pragma unroll
-      for (int f = 0; f < kInflight; ++f) {
-        const int u = ub + f * upw + sub;
-        const bool uv = u < units;
-        const int r = uv ? u / nb64 : 0;
-        const int c0 = uv ? (u - r * nb64) * 64 : 0;
-        const int c = c0 + 2 * gl;
-        const bool cv = uv && c < c0 + 64 && c < b.ldd;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) bw[f][h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
-      }
-#pragma unroll
-      for (int f = 0; f < kInflight; ++f) {
-        const int u = ub + f * upw + sub;
-        const bool uv = u < units;
-        const int r = uv ? u / nb64 : 0;
-        const int c0 = uv ? (u - r * nb64) * 64 : 0;
-        const int c = c0 + 2 * gl;
-        const bool cv = uv && c < c0 + 64 && c < b.ldd;
-        const unsigned long long* bits = bw[f];
-        if constexpr (MODE == 0 || MODE == 2) {
-            if (cv) {
-                __nv_bfloat16 hi[2], lo[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float f = __double2float_rn(__longlong_as_double((long long)bits[h]));
-                    hi[h] = __float2bfloat16_rn(f);
-                    lo[h] = __float2bfloat16_rn(f - __bfloat162float(hi[h]));
-                }
-                __nv_bfloat16* d = dest(b, r) + c;
-                store_pair(d, hi[0], hi[1]);
-                store_pair(d + b.plane, lo[0], lo[1]);
-            }
-        }
-        if constexpr (MODE == 1 || MODE == 2) {
-            const SplitDesc& e = MODE == 2 ? blocks2[blockIdx.x] : b;
-            // block maximum: non-negative doubles order like their bit patterns
-            const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFULL;
-            unsigned long long mag = max(bits[0] & kAbs, bits[1] & kAbs);
-            for (int o = G / 2; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, mag, o);
-                mag = max(mag, t);
-            }
-            const int emax = int(mag >> 52);  // biased exponent of the maximum
-            const int ex = emax - 1022;       // max < 2^ex
-            if (cv) {
-                float sc[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
-                __nv_bfloat16 sl[4][2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned long long w = bits[h];
-                    const int E = int((w >> 52) & 0x7FF);
-                    long long q = 0;
-                    if (emax > 0 && E > 0) {
-                        // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
-                        const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-                        const int sh = 21 + (emax - E);
-                        q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
-                        if (w >> 63) q = -q;
-                    }
-                    // |q| <= 2^32: the digits and every remainder after the
-                    // first fit in 32-bit integers
-                    const int m1 = int((q + (1LL << 23)) >> 24);
-                    int rem = int(q - ((long long)m1 << 24));
-                    const int m2 = (rem + (1 << 15)) >> 16;
-                    rem -= m2 << 16;
-                    const int m3 = (rem + (1 << 7)) >> 8;
-                    const int m4 = rem - (m3 << 8);
-                    sl[0][h] = __float2bfloat16_rn(float(m1) * sc[0]);
-                    sl[1][h] = __float2bfloat16_rn(float(m2) * sc[1]);
-                    sl[2][h] = __float2bfloat16_rn(float(m3) * sc[2]);
-                    sl[3][h] = __float2bfloat16_rn(float(m4) * sc[3]);
-                }
-                __nv_bfloat16* d = dest(e, r) + c;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) store_pair(d + k * e.plane, sl[k][0], sl[k][1]);
-            }
-        }
-      }
-    }
-}
-
 // partial tiles hold FP32 (hi, lo) pairs (or FP32 sums), column-pair-major:
 // element (i, j) at index ((j / 2) * BM + i) * 2 + (j % 2)
 // grid (tiles, kReduceSplit): CTA y sums rows y, y + kReduceSplit, ... of its tile
@@ -1501,9 +1343,7 @@ template <int FORM> void build_ops(Ctx& C, int side) {
         if (FORM == 2) upload_vec(d1, sd[1], st);
         for (size_t i0 = 0; i0 < sd[mlo].size(); i0 += (1u << 30)) {
             const unsigned nb = unsigned(std::min<size_t>(1u << 30, sd[mlo].size() - i0));
-            split_kernel<FORM><<<nb, 256, 0, st>>>(d0.as<SplitDesc>() + i0,
-                                                   FORM == 2 ? d1.as<SplitDesc>() + i0 : nullptr);
-            count_launch();
+            launch_split(FORM, d0.as<SplitDesc>() + i0, FORM == 2 ? d1.as<SplitDesc>() + i0 : nullptr, nb, st);
         }
         GBD_CHECK_CUDA(cudaGetLastError());
         GBD_CHECK_CUDA(cudaStreamSynchronize(st));  // the descriptor buffers are freed on return
@@ -1983,8 +1823,7 @@ template <int MODE> void run_plan(Ctx& C) {
     TcPlan& P = T.pl[MODE];
     cudaStream_t st = C.cs;
     if (P.n_psi > 0) {
-        split_kernel<MODE><<<unsigned(P.n_psi), 256, 0, st>>>(P.psi_split.as<SplitDesc>(), nullptr);
-        count_launch();
+        launch_split(MODE, P.psi_split.as<SplitDesc>(), nullptr, unsigned(P.n_psi), st);
     }
     if (P.n_w1 > 0) {
         tc_gemm_kernel<MODE, 1><<<std::min(P.n_w1, T.n_sm), THREADS, KT<MODE, 1>::SMEM_BYTES, st>>>(
@@ -2066,8 +1905,7 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
     DevBuf dsd;
     upload_vec(dsd, sd, st);
     if (!sd.empty()) {
-        split_kernel<1><<<unsigned(sd.size()), 256, 0, st>>>(dsd.as<SplitDesc>(), nullptr);
-        count_launch();
+        launch_split(1, dsd.as<SplitDesc>(), nullptr, unsigned(sd.size()), st);
     }
     std::vector<CUtensorMap> maps;
     std::vector<KSeg> segs;
@@ -2187,8 +2025,7 @@ bool tc_renormalize(Ctx& C, const OpSet& O, const Iso& U, OpSet& out, const std:
     upload_vec(dsdB, sdB, st);
     for (size_t i0 = 0; i0 < sdB.size(); i0 += (1u << 30)) {
         const unsigned n = unsigned(std::min<size_t>(1u << 30, sdB.size() - i0));
-        split_kernel<1><<<n, 256, 0, st>>>(dsdB.as<SplitDesc>() + i0, nullptr);
-        count_launch();
+        launch_split(1, dsdB.as<SplitDesc>() + i0, nullptr, n, st);
     }
     if (!worksB.empty()) {
         std::stable_sort(worksB.begin(), worksB.end(), longer);
@@ -2253,8 +2090,7 @@ void tc_enlarge_dense(Ctx& C, const std::vector<TcEnlTask>& tasks, const std::ve
     upload_vec(dsd, sd, st);
     for (size_t i0 = 0; i0 < sd.size(); i0 += (1u << 30)) {
         const unsigned n = unsigned(std::min<size_t>(1u << 30, sd.size() - i0));
-        split_kernel<1><<<n, 256, 0, st>>>(dsd.as<SplitDesc>() + i0, nullptr);
-        count_launch();
+        launch_split(1, dsd.as<SplitDesc>() + i0, nullptr, n, st);
     }
     // tensor maps (one per distinct operand), segments, work items
     std::vector<CUtensorMap> maps;
