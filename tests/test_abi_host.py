@@ -85,6 +85,21 @@ def test_config_defaults_and_validation():
         g.Context(4, 4, 0, mixed_polish=3)
     with pytest.raises(g.GbdError):
         g.Context(4, 4, 0, precision=g.SLICED_BF16)  # a product form, not a context precision
+    # the two-kernel BF16x3 form is the default; the fused kernel is an option
+    assert cfg.bf16x3_fused == 0 and cfg.autotune == 1 and cfg.low_memory == 0
+    with pytest.raises(g.GbdError):
+        g.Context(4, 4, 0, bf16x3_fused=2)
+    g.Context(4, 4, 0, bf16x3_fused=True).close()
+    # comparison forms are product forms only
+    with pytest.raises(g.GbdError):
+        g.Context(4, 4, 0, precision=g.BF16X3_FUSED)
+    # the binding's constants are the header's
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "gbdmrg.h")).read()
+    val = lambda name: int(re.search(r"\b%s\s*=?\s*(\d+)" % name, hdr).group(1))
+    assert g.BF16X3_TWO_PHASE == val("GBD_BF16X3_TWO_PHASE") and g.BF16X3_FUSED == val("GBD_BF16X3_FUSED")
+    assert g.MAX_ANCHORS == int(re.search(r"#define GBD_MAX_ANCHORS (\d+)", hdr).group(1))
 
 
 def test_timers_match_the_documented_list():
