@@ -585,6 +585,12 @@ def run_ours(args, rank, world, local_rank):
             "bytes_note": "operators read once as BF16 hi+lo (4 B/element), psi in and H psi out (FP64)",
             "hbm_view": {"achieved": gb / (f["ms"] * 1e-3), "peak": hbm, "unit": "GB/s",
                          "frac": gb / (f["ms"] * 1e-3) / hbm, "peak_source": f"{peak_src}: HBM copy bandwidth"},
+            "traffic_view": ({"achieved": traffic / (f["ms"] / n * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": traffic / (f["ms"] / n * 1e-3) / 1e9 / hbm,
+                              "peak_source": f"{peak_src}: HBM copy bandwidth",
+                              "note": "measured DRAM bytes per product (traffic) over its device time in the timed "
+                                      "steps: how close the kernel runs to HBM given the bytes it moves"}
+                             if traffic else None),
             "x_overhead_bytes_per_product": xgb / n * 1e9,
             "x_overhead_note": "two-kernel form: phase-1 intermediate X written and read once (BF16 hi+lo), "
                                "not algorithmic; 0 for the fused kernel",

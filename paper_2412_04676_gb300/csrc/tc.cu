@@ -47,6 +47,8 @@ template <int MODE, int PH> struct KT {
     static constexpr int BN = PH == 2 ? ModeCfg<MODE>::BN2 : ModeCfg<MODE>::BN;
     static constexpr int BUFCOLS = PH == 2 ? ModeCfg<MODE>::BUFCOLS2 : ModeCfg<MODE>::BUFCOLS;
     static constexpr int TMEM_COLS = PH == 2 ? ModeCfg<MODE>::TMEM_COLS2 : ModeCfg<MODE>::TMEM_COLS;
+    static constexpr int NB = TMEM_COLS / BUFCOLS;  // TMEM accumulator buffers (the MMA runs NB - 1 fills ahead)
+    static_assert(NB == 2 || NB == 4, "two or four accumulator buffers");
     // BF16x3 phase 2 sums its promotions in plain FP32 (the form's own error
     // is 2^-16); the sliced form keeps error-free (hi, lo) pairs
     static constexpr bool PAIRS = !(PH == 2 && MODE == 0);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     using K_ = KT<MODE, PH>;
     auto tile_n = [](const Work& w) { return tile_n_of<K_::BN>(w.N, w.n0); };
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[4], tempty[4];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < K_::NB; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
             mbar_init(smem_u32(&tempty[b]), EPI_WARPS);
         }
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         long long g = 0;   // chunks consumed
-        int D = 0;         // accumulator fills started (buffer D & 1)
+        int D = 0;         // accumulator fills started (buffer D % NB)
         for (int wi = blockIdx.x; wi < nworks && !vload(abort_s); wi += gridDim.x) {
             const Work w = works[wi];
             const int n = w.c1 - w.c0;
@@ -323,9 +325,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
                 }
                 if (vload(abort_s)) break;
                 tc_fence_after();
-                const int buf = D & 1;
-                if (inbuf == 0 && (D >> 1) > 0) {
-                    if (!mbar_wait(smem_u32(&tempty[buf]), uint32_t(((D >> 1) - 1) & 1))) {
+                const int buf = D % K_::NB;
+                if (inbuf == 0 && D / K_::NB > 0) {
+                    if (!mbar_wait(smem_u32(&tempty[buf]), uint32_t((D / K_::NB - 1) & 1))) {
                         atomicExch(err, 3);
                         vstore(abort_s, 1);
                         break;
@@ -405,9 +407,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Work* __restr
             for (int i = 0; i < (K_::PAIRS ? CP : 1); ++i) al[i] = 0.f;
             bool gave_up = false;
             for (int dd = 0; dd < ndrain; ++dd, ++D) {
-                const int buf = D & 1;
+                const int buf = D % K_::NB;
                 // warp-uniform outcome: the TMEM loads below are .sync.aligned
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[buf]), uint32_t((D >> 1) & 1)))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[buf]), uint32_t((D / K_::NB) & 1)))) {
                     if (lane == 0) atomicExch(err, 4);
                     vstore(abort_s, 1);
                     gave_up = true;
@@ -1227,15 +1229,20 @@ template <int MODE, int PH> double issued_gflop(const std::vector<Work>& ws, con
     for (const auto& w : ws) {
         const int v = w.N - w.n0;
         const int nn = v >= TBN ? TBN : ((v + 15) & ~15);  // the kernel's MMA width
-        // K steps of 16 the kernel issues over the item's chunks
+        // K steps of 16 the kernel issues over the item's chunks: per
+        // segment, BK / 16 for every chunk but a layer's last, which takes
+        // its remaining K rounded up to 16 (chunk j is a layer's last when
+        // (j + 1) is a multiple of the chunks per layer)
         long long ksteps = 0;
-        int s = w.seg0, c = w.c0;
-        while (s < w.seg0 + w.nseg && c >= segs[s].nchunk) { c -= segs[s].nchunk; ++s; }
-        for (int k = w.c0; k < w.c1 && s < w.seg0 + w.nseg; ++k) {
-            const int kch = (segs[s].K + BK - 1) / BK;
-            const int j0 = (c % kch) * BK;
-            ksteps += (std::max(1, std::min(BK, segs[s].K - j0)) + 15) / 16;
-            if (++c >= segs[s].nchunk) { c = 0; ++s; }
+        int s = w.seg0, a = w.c0;
+        while (s < w.seg0 + w.nseg && a >= segs[s].nchunk) { a -= segs[s].nchunk; ++s; }
+        for (int rem = w.c1 - w.c0; rem > 0 && s < w.seg0 + w.nseg; ++s, a = 0) {
+            const KSeg& g = segs[s];
+            const int b = std::min(g.nchunk, a + rem);
+            const int kch = (g.K + BK - 1) / BK;
+            const int lst = (std::max(1, std::min(BK, g.K - (kch - 1) * BK)) + 15) / 16;
+            ksteps += (long long)(BK / 16) * (b - a) - (long long)(BK / 16 - lst) * (b / kch - a / kch);
+            rem -= b - a;
         }
         f += double(ksteps) * 16.0 * BM * nn * 2.0 * (MODE == 0 ? 3.0 : 10.0);
     }
