@@ -49,7 +49,7 @@ METRIC = "H_eff psi useful TFLOP/s over whole two-site DMRG steps (mixed BF16x3 
 # bytes; valid only while the kernel source is the one that was measured.
 TRAFFIC = {
     # profiles/tc_gemm_bf16x3_l30_d1024.md: mean of nine products at cuts 14 and 15
-    "l30_d1024": {"tc_cu": "409783f885036d9b", "form": "two_phase", "bytes_per_product": 21.47e9,
+    "l30_d1024": {"tc_cu": "5efed184da78b643", "form": "two_phase", "bytes_per_product": 21.47e9,
                   "source": "profiles/tc_gemm_bf16x3_l30_d1024.md (ncu, full-size workload, one-pass metrics)"},
 }
 
