@@ -562,7 +562,7 @@ def run_ours(args, rank, world, local_rank):
         roofs["fp64"] = {"bound": "alu", "achieved": a, "peak": args.fp64_peak, "unit": "TFLOP/s",
                          "frac": a / args.fp64_peak, "traffic": None, "ms": forms["fp64"]["ms"],
                          "kernel": "gemm_f64_kernel: FP64 H_eff product (phase-1 + phase-2 launches)",
-                         "peak_source": "of measured: cuBLAS DGEMM 8192^3 on this pool"}
+                         "peak_source": "of measured: cuBLAS DGEMM 8192^3 on a GB300"}
     if "bf16x3" in forms:
         f = forms["bf16x3"]
         a, n = f["useful_tflops"], f["products"]
@@ -617,7 +617,7 @@ def run_ours(args, rank, world, local_rank):
                                  "fp64_gflop": gf64, "tensor_gflop": gftc,
                                  "kernel": "gemm_f64_kernel + copy_sum_kernel (+ tc_gemm_kernel<1, 3> for the "
                                            "sliced share): enlargement and renormalisation",
-                                 "peak_source": "of measured: cuBLAS DGEMM 8192^3 on this pool (FP64 share)"}
+                                 "peak_source": "of measured: cuBLAS DGEMM 8192^3 on a GB300 (FP64 share)"}
     # the dominant kernel by device time in the timed steps
     roof = max(roofs.values(), key=lambda r: r["ms"]) if roofs else None
     cpu = None
