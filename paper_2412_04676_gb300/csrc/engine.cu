@@ -1453,10 +1453,16 @@ int davidson(Ctx& C, double* psi_host, double* energy, gbd_dav_stats* st) {
         apply_heff_dev(C, V + size_t(k) * n, AV + size_t(k) * n, prec);
         ++nmv;
         std::vector<double> hcol;
-        dots(V, k + 1, AV + size_t(k) * n, hcol);
         if (exact0 && prec == GBD_MIXED_BF16X3) {
-            dots(AV, 1, V + size_t(k) * n, d);  // (H x) . v on the accurate side
-            hcol[0] = d[0];
+            // V^T (H v) and (H x) . v on the accurate side, one host round trip
+            multi_dot(V, n, k + 1, AV + size_t(k) * n, n, small, part, s);
+            multi_dot(AV, n, 1, V + size_t(k) * n, n, small + k + 1, part, s);
+            hcol.resize(k + 2);
+            GBD_CHECK_CUDA(cudaMemcpyAsync(hcol.data(), small, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            GBD_CHECK_CUDA(cudaStreamSynchronize(s));
+            hcol[0] = hcol[k + 1];
+        } else {
+            dots(V, k + 1, AV + size_t(k) * n, hcol);
         }
         for (int i = 0; i <= k; ++i) {
             Hs[i * kmax + k] = hcol[i];

@@ -11,11 +11,9 @@ namespace tc {
 
 namespace {
 
-
 __device__ __forceinline__ float pow2f(int e) {
     return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.f, e);
 }
-
 
 // Two adjacent BF16 values: one 4-byte store where the address allows it.
 __device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
@@ -56,100 +54,98 @@ __global__ void split_kernel(const SplitDesc* __restrict__ blocks, const SplitDe
     // row segments in flight
     constexpr int kInflight = 4;
     for (int ub = (threadIdx.x >> 5) * upw * kInflight; ub < units; ub += nw * upw * kInflight) {
-      unsigned long long bw[kInflight][2];
-      int rf[kInflight], cf[kInflight];  // row and column block of each unit (one division per group)
-      {
-        const int u = ub + sub;
-        int r = u / nb64, cb = u - r * nb64;
+        unsigned long long bw[kInflight][2];
+        int rf[kInflight], cf[kInflight];  // row and column block of each unit (one division per group)
+        {
+            const int u = ub + sub;
+            int r = u / nb64, cb = u - r * nb64;
+#pragma unroll
+            for (int f = 0; f < kInflight; ++f) {
+                rf[f] = r;
+                cf[f] = cb;
+                cb += upw;  // the next unit of this lane group: upw units further
+                while (cb >= nb64) { cb -= nb64; ++r; }
+            }
+        }
 #pragma unroll
         for (int f = 0; f < kInflight; ++f) {
-          rf[f] = r;
-          cf[f] = cb;
-          cb += upw;  // the next unit of this lane group: upw units further
-          while (cb >= nb64) { cb -= nb64; ++r; }
+            const int u = ub + f * upw + sub;
+            const bool uv = u < units;
+            const int r = uv ? rf[f] : 0;
+            const int c0 = uv ? cf[f] * 64 : 0;
+            const int c = c0 + 2 * gl;
+            const bool cv = uv && c < c0 + 64 && c < b.ldd;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) bw[f][h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
         }
-      }
 #pragma unroll
-      for (int f = 0; f < kInflight; ++f) {
-        const int u = ub + f * upw + sub;
-        const bool uv = u < units;
-        const int r = uv ? rf[f] : 0;
-        const int c0 = uv ? cf[f] * 64 : 0;
-        const int c = c0 + 2 * gl;
-        const bool cv = uv && c < c0 + 64 && c < b.ldd;
+        for (int f = 0; f < kInflight; ++f) {
+            const int u = ub + f * upw + sub;
+            const bool uv = u < units;
+            const int r = uv ? rf[f] : 0;
+            const int c0 = uv ? cf[f] * 64 : 0;
+            const int c = c0 + 2 * gl;
+            const bool cv = uv && c < c0 + 64 && c < b.ldd;
+            const unsigned long long* bits = bw[f];
+            if constexpr (MODE == 0 || MODE == 2) {
+                if (cv) {
+                    __nv_bfloat16 hi[2], lo[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) bw[f][h] = (cv && c + h < b.cols) ? src[r * b.rs + (long long)(c + h) * b.cs] : 0ULL;
-      }
-#pragma unroll
-      for (int f = 0; f < kInflight; ++f) {
-        const int u = ub + f * upw + sub;
-        const bool uv = u < units;
-        const int r = uv ? rf[f] : 0;
-        const int c0 = uv ? cf[f] * 64 : 0;
-        const int c = c0 + 2 * gl;
-        const bool cv = uv && c < c0 + 64 && c < b.ldd;
-        const unsigned long long* bits = bw[f];
-        if constexpr (MODE == 0 || MODE == 2) {
-            if (cv) {
-                __nv_bfloat16 hi[2], lo[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float f = __double2float_rn(__longlong_as_double((long long)bits[h]));
-                    hi[h] = __float2bfloat16_rn(f);
-                    lo[h] = __float2bfloat16_rn(f - __bfloat162float(hi[h]));
-                }
-                __nv_bfloat16* d = dest(b, r) + c;
-                store_pair(d, hi[0], hi[1]);
-                store_pair(d + b.plane, lo[0], lo[1]);
-            }
-        }
-        if constexpr (MODE == 1 || MODE == 2) {
-            const SplitDesc& e = MODE == 2 ? blocks2[blockIdx.x] : b;
-            // block maximum: non-negative doubles order like their bit patterns
-            const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFULL;
-            unsigned long long mag = max(bits[0] & kAbs, bits[1] & kAbs);
-            for (int o = G / 2; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, mag, o);
-                mag = max(mag, t);
-            }
-            const int emax = int(mag >> 52);  // biased exponent of the maximum
-            const int ex = emax - 1022;       // max < 2^ex
-            if (cv) {
-                float sc[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
-                __nv_bfloat16 sl[4][2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned long long w = bits[h];
-                    const int E = int((w >> 52) & 0x7FF);
-                    long long q = 0;
-                    if (emax > 0 && E > 0) {
-                        // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
-                        const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-                        const int sh = 21 + (emax - E);
-                        q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
-                        if (w >> 63) q = -q;
+                    for (int h = 0; h < 2; ++h) {
+                        const float x = __double2float_rn(__longlong_as_double((long long)bits[h]));
+                        hi[h] = __float2bfloat16_rn(x);
+                        lo[h] = __float2bfloat16_rn(x - __bfloat162float(hi[h]));
                     }
-                    // |q| <= 2^32: the digits and every remainder after the
-                    // first fit in 32-bit integers
-                    const int m1 = int((q + (1LL << 23)) >> 24);
-                    int rem = int(q - ((long long)m1 << 24));
-                    const int m2 = (rem + (1 << 15)) >> 16;
-                    rem -= m2 << 16;
-                    const int m3 = (rem + (1 << 7)) >> 8;
-                    const int m4 = rem - (m3 << 8);
-                    sl[0][h] = __float2bfloat16_rn(float(m1) * sc[0]);
-                    sl[1][h] = __float2bfloat16_rn(float(m2) * sc[1]);
-                    sl[2][h] = __float2bfloat16_rn(float(m3) * sc[2]);
-                    sl[3][h] = __float2bfloat16_rn(float(m4) * sc[3]);
+                    __nv_bfloat16* d = dest(b, r) + c;
+                    store_pair(d, hi[0], hi[1]);
+                    store_pair(d + b.plane, lo[0], lo[1]);
                 }
-                __nv_bfloat16* d = dest(e, r) + c;
+            }
+            if constexpr (MODE == 1 || MODE == 2) {
+                const SplitDesc& e = MODE == 2 ? blocks2[blockIdx.x] : b;
+                // block maximum: non-negative doubles order like their bit
+                // patterns; only its exponent is used, and that sits in the
+                // high 32 bits, so the group reduces those
+                unsigned int mag = max(unsigned(bits[0] >> 32) & 0x7FFFFFFFu, unsigned(bits[1] >> 32) & 0x7FFFFFFFu);
+                for (int o = G / 2; o > 0; o >>= 1) mag = max(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+                const int emax = int(mag >> 20);  // biased exponent of the maximum
+                const int ex = emax - 1022;       // max < 2^ex
+                if (cv) {
+                    float sc[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) store_pair(d + k * e.plane, sl[k][0], sl[k][1]);
+                    for (int k = 0; k < 4; ++k) sc[k] = pow2f(ex - 8 * (k + 1));
+                    __nv_bfloat16 sl[4][2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const unsigned long long w = bits[h];
+                        const int E = int((w >> 52) & 0x7FF);
+                        long long q = 0;
+                        if (emax > 0 && E > 0) {
+                            // x = M 2^(E-1075), q = round(M 2^-s) with s = 21 + (emax - E) >= 21
+                            const unsigned long long M = (w & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+                            const int sh = 21 + (emax - E);
+                            q = sh >= 64 ? 0 : (long long)((M + (1ULL << (sh - 1))) >> sh);
+                            if (w >> 63) q = -q;
+                        }
+                        // |q| <= 2^32: the digits and every remainder after
+                        // the first fit in 32-bit integers
+                        const int m1 = int((q + (1LL << 23)) >> 24);
+                        int rem = int(q - ((long long)m1 << 24));
+                        const int m2 = (rem + (1 << 15)) >> 16;
+                        rem -= m2 << 16;
+                        const int m3 = (rem + (1 << 7)) >> 8;
+                        const int m4 = rem - (m3 << 8);
+                        sl[0][h] = __float2bfloat16_rn(float(m1) * sc[0]);
+                        sl[1][h] = __float2bfloat16_rn(float(m2) * sc[1]);
+                        sl[2][h] = __float2bfloat16_rn(float(m3) * sc[2]);
+                        sl[3][h] = __float2bfloat16_rn(float(m4) * sc[3]);
+                    }
+                    __nv_bfloat16* d = dest(e, r) + c;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) store_pair(d + k * e.plane, sl[k][0], sl[k][1]);
+                }
             }
         }
-      }
     }
 }
 
