@@ -1526,10 +1526,6 @@ struct Pick {
 // dir = +1: keep states of the enlarged left block, new left-isometric site b,
 // new left environment at cut b+1, start vector at b+1.  dir = -1: the
 // mirror image on the right, start vector at b-1.
-// Density matrices of kEigDC rows or more are diagonalised one at a time by
-// divide and conquer rather than in a batch.
-constexpr int kEigDC = 192;
-
 double truncate_step(Ctx& C, int dir, int Dmax) {
     Heff& H = C.H;
     const int b = H.b;
@@ -1607,10 +1603,8 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     P.check({{C.psi.p, C.psi.bytes}, {rho.p, rho.bytes}}, "truncate/rho");
     P.upload(s);
     P.launch(s);
-    // eigen-decomposition (FP64, cuSOLVER): one batched solve per size class of
-    // small matrices, divide and conquer per matrix for the large ones
-    // (kEigDC rows and up, which a class holds one or two of); the classes
-    // spread over several streams (largest first) so they overlap
+    // eigen-decomposition (FP64, cuSOLVER): one batched solve per size class,
+    // the classes spread over several streams (largest first) so they overlap
     const double t_eig0 = wall_ms();
     cudaEvent_t e_rho;
     GBD_CHECK_CUDA(cudaEventCreateWithFlags(&e_rho, cudaEventDisableTiming));
@@ -1624,17 +1618,11 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
         const EigClass& ec = ecls[corder[j]];
         const int k = int(j % Ctx::kEigStreams);
         size_t wd = 0, wh = 0;
-        if (ec.n >= kEigDC) {
-            if (cusolverDnXsyevd_bufferSize(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ec.n,
-                                            CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F,
-                                            evals.as<double>() + ec.w0, CUDA_R_64F, &wd, &wh) != CUSOLVER_STATUS_SUCCESS)
-                throw Error(GBD_ERR_CUDA, "syevd buffer size query failed");
-        } else if (cusolverDnXsyevBatched_bufferSize(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR,
-                                                     CUBLAS_FILL_MODE_LOWER, ec.n, CUDA_R_64F, rho.as<double>() + ec.a0,
-                                                     ec.n, CUDA_R_64F, evals.as<double>() + ec.w0, CUDA_R_64F, &wd, &wh,
-                                                     ec.batch) != CUSOLVER_STATUS_SUCCESS) {
+        if (cusolverDnXsyevBatched_bufferSize(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                              ec.n, CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F,
+                                              evals.as<double>() + ec.w0, CUDA_R_64F, &wd, &wh,
+                                              ec.batch) != CUSOLVER_STATUS_SUCCESS)
             throw Error(GBD_ERR_CUDA, "batched syev buffer size query failed");
-        }
         wd_need[k] = std::max(wd_need[k], wd);
         wh_need[k] = std::max(wh_need[k], wh);
     }
@@ -1646,23 +1634,12 @@ double truncate_step(Ctx& C, int dir, int Dmax) {
     for (size_t j = 0; j < corder.size(); ++j) {
         const EigClass& ec = ecls[corder[j]];
         const int k = int(j % Ctx::kEigStreams);
-        if (ec.n >= kEigDC) {
-            for (int q = 0; q < ec.batch; ++q) {  // one matrix at a time, the class's slots in order
-                const long long nn = (long long)ec.n * ec.n;
-                if (cusolverDnXsyevd(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ec.n,
-                                     CUDA_R_64F, rho.as<double>() + ec.a0 + q * nn, ec.n, CUDA_R_64F,
-                                     evals.as<double>() + ec.w0 + (long long)q * ec.n, CUDA_R_64F, C.eig_work[k].p,
-                                     C.eig_work[k].bytes, C.eig_host[k].empty() ? nullptr : C.eig_host[k].data(),
-                                     C.eig_host[k].size(), info.as<int>() + ec.i0 + q) != CUSOLVER_STATUS_SUCCESS)
-                    throw Error(GBD_ERR_CUDA, "syevd failed");
-            }
-        } else if (cusolverDnXsyevBatched(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                          ec.n, CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F,
-                                          evals.as<double>() + ec.w0, CUDA_R_64F, C.eig_work[k].p, C.eig_work[k].bytes,
-                                          C.eig_host[k].empty() ? nullptr : C.eig_host[k].data(), C.eig_host[k].size(),
-                                          info.as<int>() + ec.i0, ec.batch) != CUSOLVER_STATUS_SUCCESS) {
+        if (cusolverDnXsyevBatched(C.eig_sol[k], C.eig_params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ec.n,
+                                   CUDA_R_64F, rho.as<double>() + ec.a0, ec.n, CUDA_R_64F, evals.as<double>() + ec.w0,
+                                   CUDA_R_64F, C.eig_work[k].p, C.eig_work[k].bytes,
+                                   C.eig_host[k].empty() ? nullptr : C.eig_host[k].data(), C.eig_host[k].size(),
+                                   info.as<int>() + ec.i0, ec.batch) != CUSOLVER_STATUS_SUCCESS)
             throw Error(GBD_ERR_CUDA, "batched syev failed");
-        }
     }
     for (int k = 0; k < Ctx::kEigStreams; ++k) {
         cudaEvent_t e;
